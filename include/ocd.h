@@ -1,0 +1,112 @@
+/*
+ * ocd.h -- C ABI of the GB300 (sm_103a) OCD soft-output MU-MIMO-OFDM detector.
+ *
+ * Method: optimized coordinate descent (OCD), Algorithm 1 of Wu, Dick,
+ * Cavallaro, Studer, "High-Throughput Data Detection for Massive MU-MIMO-OFDM
+ * using Coordinate Descent" (arXiv 1611.08779), with the max-log LLRs of Eq. 9
+ * under the soft-output approximation of Section III-C.
+ *
+ * Problem per subcarrier w and OFDM symbol t (system model, Eq. 1):
+ *     y_{w,t} = H_w s_{w,t} + n,   H_w in C^{B x U},  n ~ CN(0, N0 I_B),
+ *     E|s|^2 = Es, s drawn from a Gray-labelled square QAM (or BPSK) alphabet.
+ *
+ * Data layout (all arrays row-major, C-contiguous, complex = interleaved
+ * float32 (re, im), i.e. C99 `float _Complex` / torch.complex64):
+ *     H     complex [Nsc][B][U]        channel, shared by the T symbols
+ *     Y     complex [Nsc][T][B]        received vectors
+ *     xhat  complex [Nsc][T][U]        equalizer output z^(K)     (optional)
+ *     llr   float   [Nsc][T][U][Q]     max-log LLRs, Q = log2(order) (optional)
+ * LLR bit order: for square QAM the first Q/2 bits (most significant first)
+ * label the in-phase level and the next Q/2 the quadrature level, each a
+ * binary-reflected Gray word over levels ordered from most negative to most
+ * positive.  Sign: L > 0 favours bit 1 (Eq. 9 as printed).
+ *
+ * Modes (Algorithm 1, initialization): OCD_MMSE uses alpha = N0/Es and no
+ * projection; OCD_BOX uses alpha = 0 and clips the real and imaginary parts
+ * to [-a, a], a = sqrt(Es) * max Re{O} (Eq. 14 and Section II-D); for BPSK
+ * the imaginary part is set to zero.
+ *
+ * Soft output (Section III-C): mu~_u = p_u = ||h_u||^2 / (||h_u||^2 + alpha),
+ * rho~_u = ||h_u||^2 Es / N0 (equal to mu~/(1-mu~) in MMSE mode, and its
+ * finite reading in BOX mode), LLRs taken on z_u / (mu~_u sqrt(Es)) against
+ * the unit-energy alphabet.  A user whose column is zero gets z = 0, L = 0.
+ *
+ * Threading and ownership: device pointers are owned by the caller.  The
+ * device entry points allocate nothing, never synchronize, and enqueue their
+ * work on `stream` (0 = legacy default stream).  Errors are reported by the
+ * return value; ocd_last_error() gives a message for the calling thread.
+ */
+#ifndef OCD_H_
+#define OCD_H_
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
+
+typedef enum {
+  OCD_OK = 0,
+  OCD_ERR_ARG = -1,          /* invalid argument; nothing was enqueued          */
+  OCD_ERR_UNSUPPORTED = -2,  /* valid but outside the implemented limits        */
+  OCD_ERR_CUDA = -3          /* a CUDA runtime call or the launch failed        */
+} ocd_status_t;
+
+/* Limits (mirroring the run-time parameters of Section IV: U <= 32, K <= 256). */
+#define OCD_MAX_USERS 32
+#define OCD_MAX_ANTENNAS 512
+#define OCD_MAX_SWEEPS 256
+
+/*
+ * ocd_detect -- Algorithm 1 (preprocessing, K sweeps of h_u^H r, scalar
+ * update with projection, residual update r -= h_u dz) followed by Eq. 9.
+ *
+ *   H, Y        device pointers, layouts above.  Must not be NULL when
+ *               Nsc*T > 0.  8-byte alignment is required; 16-byte alignment
+ *               (and even B) enables vector loads.
+ *   Nsc, T      subcarriers and symbols per subcarrier, >= 0 (0 = nothing to do).
+ *   B, U        antennas 1..OCD_MAX_ANTENNAS, users 1..OCD_MAX_USERS.
+ *   N0, Es      noise variance (>= 0) and symbol energy (> 0).  N0 must be
+ *               > 0 when llr != NULL; N0 == 0 in MMSE mode gives plain
+ *               least-squares coordinate descent.
+ *   K           sweeps 0..OCD_MAX_SWEEPS (0 gives z = 0).
+ *   mode        OCD_MMSE or OCD_BOX.
+ *   qam_order   2 (BPSK), 4, 16, 64 or 256.
+ *   xhat, llr   device outputs; either may be NULL but not both.
+ * Returns OCD_OK, OCD_ERR_ARG, OCD_ERR_UNSUPPORTED or OCD_ERR_CUDA.
+ */
+int ocd_detect(const void* H, const void* Y, int Nsc, int B, int U, int T,
+               float N0, float Es, int K, int mode, int qam_order,
+               void* xhat, float* llr, cudaStream_t stream);
+
+/*
+ * ocd_detect_host -- the same computation on HOST buffers (Eq. 1 inputs in,
+ * Algorithm 1 + Eq. 9 outputs out).  Copies H and Y to the caller-supplied
+ * device buffers dH, dY (same sizes as H, Y), runs ocd_detect into dX / dL,
+ * and copies the results back to xhat / llr on the host.  Pinned host memory
+ * is needed for the copies to overlap with compute.  The subcarriers are
+ * processed in `pieces` consecutive slices (1..64) so that the copies of one
+ * slice overlap the kernel of another; the library uses an internal pair of
+ * streams per device, ordered after `stream` on entry and before it on exit.
+ * A NULL host output skips that output (its device buffer may then be NULL).
+ * Nothing is synchronized: the host results are valid once `stream` is.
+ */
+int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T,
+                    float N0, float Es, int K, int mode, int qam_order,
+                    void* xhat, float* llr,
+                    void* dH, void* dY, void* dX, float* dL,
+                    int pieces, cudaStream_t stream);
+
+/* Message describing the last non-OK status returned on the calling thread. */
+const char* ocd_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int ocd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCD_H_ */

@@ -1,1 +1,9 @@
-"""GB300-native OCD soft-output detection for massive MU-MIMO-OFDM."""
+"""GB300-native OCD soft-output detection for massive MU-MIMO-OFDM.
+
+The detector (Algorithm 1 of arXiv 1611.08779 with the Eq. 9 soft output)
+runs in the CUDA library libocd.so; this package is its Python binding plus
+the seeded input generator and the subcarrier partition used by the benchmark.
+"""
+from ._native import OcdError  # noqa: F401
+from .api import bits_per_symbol, make_staging, ocd_detect, ocd_detect_host, version  # noqa: F401
+from .shard import shard_range  # noqa: F401

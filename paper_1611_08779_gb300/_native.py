@@ -1,0 +1,70 @@
+"""ctypes loader for libocd.so (the C ABI declared in include/ocd.h).
+
+There is no fallback: if the library is missing or cannot be loaded, every
+call raises.  Build it with `python -m paper_1611_08779_gb300.build`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB_PATH
+
+OCD_OK = 0
+OCD_ERR_ARG = -1
+OCD_ERR_UNSUPPORTED = -2
+OCD_ERR_CUDA = -3
+OCD_MMSE = 0
+OCD_BOX = 1
+OCD_MAX_USERS = 32
+OCD_MAX_ANTENNAS = 512
+OCD_MAX_SWEEPS = 256
+
+_STATUS = {OCD_ERR_ARG: "OCD_ERR_ARG", OCD_ERR_UNSUPPORTED: "OCD_ERR_UNSUPPORTED",
+           OCD_ERR_CUDA: "OCD_ERR_CUDA"}
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_f = ctypes.c_float
+
+SIGNATURES = {
+    "ocd_detect": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp, _vp]),
+    "ocd_detect_host": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp,
+                             _vp, _vp, _vp, _vp, _i, _vp]),
+    "ocd_last_error": (ctypes.c_char_p, []),
+    "ocd_version": (_i, []),
+}
+
+
+class OcdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libocd.so once and declare its prototypes."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{os.path.basename(path)} is not built; run "
+                    "`python -m paper_1611_08779_gb300.build` (the detector has no CPU path)")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != OCD_OK:
+        msg = load().ocd_last_error()
+        raise OcdError(status, msg.decode() if msg else "")

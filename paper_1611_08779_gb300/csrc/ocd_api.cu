@@ -1,0 +1,343 @@
+// C ABI of the OCD detector: argument validation, launch planning and
+// dispatch to the sm_103a kernels.  See include/ocd.h for the contract.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "ocd.h"
+#include "ocd_common.cuh"
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+constexpr int kMaxDevices = 64;
+constexpr size_t kSmemBudget = 72 * 1024;  // preferred per-CTA budget: >= 3 CTAs per SM
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(OCD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+int pow2_ceil(int v) { return 1 << ilog2(v < 1 ? 1 : v); }
+
+// ---------------------------------------------------------------------------
+// Constellation constants (Section II-A, II-D)
+// ---------------------------------------------------------------------------
+struct Alphabet {
+  int Q, nb, M, bpsk;
+  double step;    // 1/sigma
+  double radius;  // max Re{O} at unit energy
+};
+
+bool alphabet_of(int order, Alphabet& a) {
+  switch (order) {
+    case 2: a = {1, 1, 2, 1, 1.0, 1.0}; return true;
+    case 4: case 16: case 64: case 256: {
+      const int Q = order == 4 ? 2 : order == 16 ? 4 : order == 64 ? 6 : 8;
+      const int M = 1 << (Q / 2);
+      const double sigma = sqrt(2.0 * (M * M - 1) / 3.0);
+      a = {Q, Q / 2, M, 0, 1.0 / sigma, (M - 1) / sigma};
+      return true;
+    }
+    default: return false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel table: UMAX in {4, 8, 16, 32} x NPP in {2, 4, 8, 16}
+// ---------------------------------------------------------------------------
+using ocd::KernelFn;
+
+KernelFn pick_kernel(int umax, int npp) {
+  switch (umax) {
+    case 4: return ocd::residual_kernel_u4(npp);
+    case 8: return ocd::residual_kernel_u8(npp);
+    case 16: return ocd::residual_kernel_u16(npp);
+    default: return ocd::residual_kernel_u32(npp);
+  }
+}
+
+struct DeviceInfo {
+  bool ready = false;
+  int sms = 0;
+  size_t smem_optin = 0;  // largest dynamic shared memory a CTA may opt into
+};
+DeviceInfo g_dev[kMaxDevices];
+std::mutex g_dev_mu;
+
+int device_info(int dev, DeviceInfo& out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(OCD_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_dev[dev].ready) {
+    int sms = 0, optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const int umaxes[4] = {4, 8, 16, 32};
+    const int npps[4] = {2, 4, 8, 16};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        e = cudaFuncSetAttribute(pick_kernel(umaxes[a], npps[b]),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      }
+    g_dev[dev].sms = sms;
+    g_dev[dev].smem_optin = (size_t)optin;
+    g_dev[dev].ready = true;
+  }
+  out = g_dev[dev];
+  return OCD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch plan
+// ---------------------------------------------------------------------------
+struct Plan {
+  int umax, npp, L, nt;
+  size_t smem;
+};
+
+size_t smem_bytes(int scmax, int sc_stride) {
+  return (size_t)scmax * sc_stride * sizeof(float2) + (size_t)scmax * ocd::kUserSlots * 3 * sizeof(float);
+}
+
+// Prefer the fewest lanes per item (fewest shuffles per inner product) whose
+// staged channels fit the shared-memory budget.
+int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl) {
+  pl.umax = U <= 4 ? 4 : U <= 8 ? 8 : U <= 16 ? 16 : 32;
+  const int npp_cap = pl.umax >= 32 ? 8 : 16;
+  const int pairs = (B + 1) / 2;
+  int L = 1;
+  while (L * npp_cap < pairs) L <<= 1;
+  int nt = 128;
+  for (;;) {
+    if (L > 32) return fail(OCD_ERR_UNSUPPORTED, "B=%d U=%d does not fit the team layout", B, U);
+    int npp = pow2_ceil((pairs + L - 1) / L);
+    if (npp < 2) npp = 2;
+    const int teams = nt / L;
+    const int chunk = teams;
+    int scmax = (chunk - 1 + T - 1) / T + 1;
+    if (scmax > chunk) scmax = chunk;
+    const int rs = 2 * L * npp + 2;
+    const int sc_stride = U * rs + 8;
+    const size_t sm = smem_bytes(scmax, sc_stride);
+    if (sm <= budget) {
+      pl.npp = npp; pl.L = L; pl.nt = nt; pl.smem = sm;
+      P.L = L; P.logL = ilog2(L); P.chunk = chunk; P.scmax = scmax;
+      P.rs = rs; P.sc_stride = sc_stride;
+      return OCD_OK;
+    }
+    if (L < 32) L <<= 1;
+    else if (nt > 32) nt >>= 1;
+    else return fail(OCD_ERR_UNSUPPORTED, "B=%d U=%d: one subcarrier exceeds shared memory", B, U);
+  }
+}
+
+int validate(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
+             int K, int mode, int qam_order, const void* xhat, const void* llr, Alphabet& al) {
+  if (Nsc < 0 || T < 0) return fail(OCD_ERR_ARG, "Nsc=%d and T=%d must be >= 0", Nsc, T);
+  if (B < 1 || B > OCD_MAX_ANTENNAS) return fail(OCD_ERR_ARG, "B=%d outside 1..%d", B, OCD_MAX_ANTENNAS);
+  if (U < 1 || U > OCD_MAX_USERS) return fail(OCD_ERR_ARG, "U=%d outside 1..%d", U, OCD_MAX_USERS);
+  if (K < 0 || K > OCD_MAX_SWEEPS) return fail(OCD_ERR_ARG, "K=%d outside 0..%d", K, OCD_MAX_SWEEPS);
+  if (mode != OCD_MMSE && mode != OCD_BOX) return fail(OCD_ERR_ARG, "unknown mode %d", mode);
+  if (!alphabet_of(qam_order, al)) return fail(OCD_ERR_ARG, "unsupported qam_order %d", qam_order);
+  if (!(Es > 0.0f) || !isfinite(Es)) return fail(OCD_ERR_ARG, "Es must be finite and > 0");
+  if (!(N0 >= 0.0f) || !isfinite(N0)) return fail(OCD_ERR_ARG, "N0 must be finite and >= 0");
+  if (!xhat && !llr) return fail(OCD_ERR_ARG, "both outputs are NULL");
+  if (llr && !(N0 > 0.0f)) return fail(OCD_ERR_ARG, "LLRs need N0 > 0 (rho~ = ||h||^2 Es/N0)");
+  const long long items = (long long)Nsc * T;
+  if (items > 0 && (!H || !Y)) return fail(OCD_ERR_ARG, "H and Y must not be NULL");
+  if (((uintptr_t)H | (uintptr_t)Y | (uintptr_t)xhat) & 7u)
+    return fail(OCD_ERR_ARG, "complex arrays must be 8-byte aligned");
+  if ((uintptr_t)llr & 3u) return fail(OCD_ERR_ARG, "llr must be 4-byte aligned");
+  return OCD_OK;
+}
+
+int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
+                  int K, int mode, const Alphabet& al, void* xhat, float* llr, cudaStream_t stream) {
+  const long long items = (long long)Nsc * T;
+  if (items == 0) return OCD_OK;
+  ocd::DetectParams P;
+  memset(&P, 0, sizeof(P));
+  P.H = static_cast<const float2*>(H);
+  P.Y = static_cast<const float2*>(Y);
+  P.xhat = static_cast<float2*>(xhat);
+  P.llr = llr;
+  P.items = items;
+  P.Nsc = Nsc; P.B = B; P.U = U; P.T = T; P.K = K;
+  P.box = mode == OCD_BOX;
+  P.bpsk = al.bpsk;
+  P.Q = al.Q; P.nb = al.nb; P.M = al.M;
+  P.alpha = mode == OCD_MMSE ? (float)((double)N0 / (double)Es) : 0.0f;
+  P.sqrt_es = (float)sqrt((double)Es);
+  P.box_a = (float)(al.radius * sqrt((double)Es));
+  P.rho_scale = N0 > 0.0f ? (float)((double)Es / (double)N0) : 0.0f;
+  P.lvl_step = (float)al.step;
+  P.vec_y = (B % 2 == 0) && (((uintptr_t)Y & 15u) == 0);
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  DeviceInfo di;
+  int st = device_info(dev, di);
+  if (st != OCD_OK) return st;
+
+  // Keep several CTAs per SM when the staged channels allow it; otherwise
+  // take up to the whole opt-in shared memory of one CTA.
+  Plan pl;
+  st = make_plan(B, U, T, kSmemBudget, P, pl);
+  if (st != OCD_OK) st = make_plan(B, U, T, di.smem_optin, P, pl);
+  if (st != OCD_OK) return st;
+
+  KernelFn fn = pick_kernel(pl.umax, pl.npp);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, pl.nt, pl.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (per_sm < 1) return fail(OCD_ERR_UNSUPPORTED, "kernel cannot be resident (smem %zu)", pl.smem);
+  const long long nchunks = (items + P.chunk - 1) / P.chunk;
+  long long grid = (long long)di.sms * per_sm;
+  if (grid > nchunks) grid = nchunks;
+  void* args[] = {&P};
+  e = cudaLaunchKernel((const void*)fn, dim3((unsigned)grid), dim3(pl.nt), args, pl.smem, stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return OCD_OK;
+}
+
+// Internal streams of ocd_detect_host (one pair per device, created once).
+struct HostStreams {
+  bool ready = false;
+  cudaStream_t s[2];
+  cudaEvent_t ev_in, ev_out[2];
+};
+HostStreams g_hs[kMaxDevices];
+std::mutex g_hs_mu;
+
+// Caller holds g_hs_mu.
+int host_streams(int dev, HostStreams*& out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(OCD_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+  HostStreams& h = g_hs[dev];
+  if (!h.ready) {
+    cudaError_t e;
+    for (int i = 0; i < 2; ++i) {
+      e = cudaStreamCreateWithFlags(&h.s[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+      e = cudaEventCreateWithFlags(&h.ev_out[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
+    }
+    e = cudaEventCreateWithFlags(&h.ev_in, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
+    h.ready = true;
+  }
+  out = &h;
+  return OCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ocd_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
+               int K, int mode, int qam_order, void* xhat, float* llr, cudaStream_t stream) {
+  Alphabet al;
+  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, al);
+  if (st != OCD_OK) return st;
+  return launch_detect(H, Y, Nsc, B, U, T, N0, Es, K, mode, al, xhat, llr, stream);
+}
+
+int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
+                    int K, int mode, int qam_order, void* xhat, float* llr, void* dH, void* dY,
+                    void* dX, float* dL, int pieces, cudaStream_t stream) {
+  Alphabet al;
+  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, al);
+  if (st != OCD_OK) return st;
+  if (pieces < 1 || pieces > 64) return fail(OCD_ERR_ARG, "pieces=%d outside 1..64", pieces);
+  const long long items = (long long)Nsc * T;
+  if (items == 0) return OCD_OK;
+  if (!dH || !dY) return fail(OCD_ERR_ARG, "device staging buffers dH, dY must not be NULL");
+  if (xhat && !dX) return fail(OCD_ERR_ARG, "xhat requested but dX is NULL");
+  if (llr && !dL) return fail(OCD_ERR_ARG, "llr requested but dL is NULL");
+  if (((uintptr_t)dH | (uintptr_t)dY | (uintptr_t)dX) & 7u || ((uintptr_t)dL & 3u))
+    return fail(OCD_ERR_ARG, "device staging buffers are misaligned");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // The internal streams and events are shared by every caller on this
+  // device, so the whole enqueue sequence runs under one lock.
+  std::lock_guard<std::mutex> lk(g_hs_mu);
+  HostStreams* hs = nullptr;
+  st = host_streams(dev, hs);
+  if (st != OCD_OK) return st;
+
+  e = cudaEventRecord(hs->ev_in, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  for (int i = 0; i < 2; ++i) {
+    e = cudaStreamWaitEvent(hs->s[i], hs->ev_in, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  if (pieces > Nsc) pieces = Nsc > 0 ? Nsc : 1;
+  const size_t hsz = (size_t)B * U * sizeof(float2);
+  const size_t ysz = (size_t)T * B * sizeof(float2);
+  const size_t xsz = (size_t)T * U * sizeof(float2);
+  const size_t lsz = (size_t)T * U * al.Q * sizeof(float);
+  for (int p = 0; p < pieces; ++p) {
+    const long long a = (long long)Nsc * p / pieces;
+    const long long b = (long long)Nsc * (p + 1) / pieces;
+    const int n = (int)(b - a);
+    if (n == 0) continue;
+    cudaStream_t s = hs->s[p & 1];
+    char* dh = static_cast<char*>(dH) + a * hsz;
+    char* dy = static_cast<char*>(dY) + a * ysz;
+    e = cudaMemcpyAsync(dh, static_cast<const char*>(H) + a * hsz, n * hsz, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H");
+    e = cudaMemcpyAsync(dy, static_cast<const char*>(Y) + a * ysz, n * ysz, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync Y");
+    char* dx = xhat ? static_cast<char*>(dX) + a * xsz : nullptr;
+    float* dl = llr ? reinterpret_cast<float*>(reinterpret_cast<char*>(dL) + a * lsz) : nullptr;
+    st = launch_detect(dh, dy, n, B, U, T, N0, Es, K, mode, al, dx, dl, s);
+    if (st != OCD_OK) return st;
+    if (xhat) {
+      e = cudaMemcpyAsync(static_cast<char*>(xhat) + a * xsz, dx, n * xsz, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync xhat");
+    }
+    if (llr) {
+      e = cudaMemcpyAsync(reinterpret_cast<char*>(llr) + a * lsz, dl, n * lsz, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync llr");
+    }
+  }
+  for (int i = 0; i < 2; ++i) {
+    e = cudaEventRecord(hs->ev_out[i], hs->s[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    e = cudaStreamWaitEvent(stream, hs->ev_out[i], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  return OCD_OK;
+}
+
+const char* ocd_last_error(void) { return g_err; }
+
+int ocd_version(void) { return kVersion; }
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.  Tolerances in tests/parity.py."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc  # noqa: E402
+import paper_1611_08779_gb300 as ocd  # noqa: E402
+from paper_1611_08779_gb300 import synth  # noqa: E402
+
+from .parity import assert_parity, xhat_error  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MODE = {orc.MMSE: "mmse", orc.BOX: "box"}
+
+
+def run_gpu(d, K, mode, order, Es=1.0, N0=None, want_xhat=True, want_llr=True):
+    H = torch.from_numpy(d["H"]).cuda()
+    Y = torch.from_numpy(d["Y"]).cuda()
+    x, L = ocd.ocd_detect(H, Y, d["N0"] if N0 is None else N0, Es, K, MODE[mode], order,
+                          want_xhat=want_xhat, want_llr=want_llr)
+    torch.cuda.synchronize()
+    return (x.cpu().numpy() if x is not None else None,
+            L.cpu().numpy() if L is not None else None)
+
+
+def check(Nsc, B, U, T, K, mode, order, snr, seed, Es=1.0, label=""):
+    d = synth.make_uplink(Nsc, B, U, T, order, snr, seed, Es=Es)
+    x, L = run_gpu(d, K, mode, order, Es)
+    return assert_parity(x, L, d["H"], d["Y"], d["N0"], Es, K, mode, order, label)
+
+
+# Small configuration of the paper's 32x8 system: 64 subcarriers, T = 1, K = 3,
+# 16-QAM at 10 dB, OCD-MMSE.
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_32x8_16qam_t1(mode):
+    check(64, 32, 8, 1, 3, mode, 16, 10.0, 0, label="32x8")
+
+
+# The 128x8 64-QAM K=3 T=14 system over the SNR sweep (a slice of subcarriers).
+@pytest.mark.parametrize("snr", [0.0, 10.0, 20.0, 30.0])
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_128x8_64qam_t14_snr_sweep(mode, snr):
+    check(24, 128, 8, 14, 3, mode, 64, snr, int(snr) + 1, label=f"128x8 {snr}dB")
+
+
+@pytest.mark.parametrize("order", [2, 4, 16, 64, 256])
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_every_alphabet(mode, order):
+    check(9, 64, 6, 5, 4, mode, order, 18.0, 3, label=f"order {order}")
+
+
+# Ragged shapes: odd B (scalar Y loads, padded antennas), U not a power of
+# two, T not dividing the CTA chunk, many chunks with a partial last one.
+@pytest.mark.parametrize("B,U,T,Nsc", [
+    (37, 5, 3, 29), (1, 1, 1, 5), (3, 2, 7, 11), (4, 8, 2, 6), (130, 7, 13, 17),
+    (200, 12, 9, 10), (96, 16, 14, 8), (64, 32, 3, 5), (256, 16, 14, 6),
+    (512, 32, 2, 3), (512, 1, 5, 4), (33, 17, 1, 40), (17, 3, 33, 3)])
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_ragged_shapes(mode, B, U, T, Nsc):
+    check(Nsc, B, U, T, 3, mode, 16, 12.0, B * 7 + U, label=f"{B}x{U} T{T}")
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 5, 16])
+def test_sweep_counts(K):
+    check(10, 48, 6, 4, K, orc.MMSE, 64, 15.0, 40 + K, label=f"K={K}")
+    check(10, 48, 6, 4, K, orc.BOX, 64, 5.0, 50 + K, label=f"K={K}")
+
+
+def test_maximum_sweeps_box():
+    check(3, 16, 4, 2, 256, orc.BOX, 16, 5.0, 60, label="K=256")
+
+
+def test_symbol_energy_not_one():
+    check(8, 64, 8, 6, 3, orc.MMSE, 64, 12.0, 61, Es=2.5)
+    check(8, 64, 8, 6, 3, orc.BOX, 16, 12.0, 62, Es=0.3)
+
+
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_zero_column(mode):
+    d = synth.make_uplink(6, 32, 5, 3, 16, 10.0, 63)
+    d["H"][:, :, 3] = 0
+    d["H"][2, :, 0] = 0
+    x, L = run_gpu(d, 3, mode, 16)
+    assert np.all(x[:, :, 3] == 0) and np.all(L[:, :, 3] == 0)
+    assert_parity(x, L, d["H"], d["Y"], d["N0"], 1.0, 3, mode, 16)
+
+
+def test_least_squares_mmse_with_zero_noise():
+    d = synth.make_uplink(5, 64, 8, 3, 64, 20.0, 64)
+    x, L = run_gpu(d, 6, orc.MMSE, 64, N0=0.0, want_llr=False)
+    assert L is None
+    z_ref, *_ = orc.ocd_equalize(d["H"], d["Y"], 0.0, 1.0, 6, orc.MMSE, 64)
+    assert xhat_error(x, z_ref) <= 1e-4
+
+
+def test_outputs_optional():
+    d = synth.make_uplink(5, 32, 4, 3, 16, 10.0, 65)
+    x1, L1 = run_gpu(d, 3, orc.BOX, 16)
+    x2, L2 = run_gpu(d, 3, orc.BOX, 16, want_llr=False)
+    x3, L3 = run_gpu(d, 3, orc.BOX, 16, want_xhat=False)
+    assert L2 is None and x3 is None
+    assert np.array_equal(x1, x2) and np.array_equal(L1, L3)
+
+
+def test_empty_inputs():
+    H = torch.zeros((0, 16, 4), dtype=torch.complex64, device="cuda")
+    Y = torch.zeros((0, 3, 16), dtype=torch.complex64, device="cuda")
+    x, L = ocd.ocd_detect(H, Y, 0.1, qam_order=16)
+    assert x.shape == (0, 3, 4) and L.shape == (0, 3, 4, 4)
+    H = torch.zeros((4, 16, 4), dtype=torch.complex64, device="cuda")
+    Y = torch.zeros((4, 0, 16), dtype=torch.complex64, device="cuda")
+    x, L = ocd.ocd_detect(H, Y, 0.1, qam_order=16)
+    torch.cuda.synchronize()
+    assert x.shape == (4, 0, 4)
+
+
+def test_noiseless_recovery_on_gpu():
+    d = synth.make_noiseless(16, 128, 8, 14, 64, seed=66)
+    d["H"] = d["H"].astype(np.complex64)
+    d["Y"] = d["Y"].astype(np.complex64)
+    d["N0"] = 1e-6
+    x, L = run_gpu(d, 8, orc.BOX, 64)
+    assert np.array_equal((L > 0).astype(np.uint8), d["bits"])
+
+
+def test_deterministic_and_stream_independent():
+    d = synth.make_uplink(40, 128, 8, 14, 64, 15.0, 67)
+    H = torch.from_numpy(d["H"]).cuda()
+    Y = torch.from_numpy(d["Y"]).cuda()
+    x1, L1 = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "box", 64)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        x2, L2 = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "box", 64)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2) and torch.equal(L1, L2)
+
+
+def test_unaligned_y_uses_scalar_loads():
+    # Y starting 8 bytes past a 16-byte boundary takes the scalar-load path
+    d = synth.make_uplink(6, 64, 8, 3, 16, 10.0, 68)
+    H = torch.from_numpy(d["H"]).cuda()
+    flat = torch.zeros(d["Y"].size + 1, dtype=torch.complex64, device="cuda")
+    flat[1:] = torch.from_numpy(d["Y"].reshape(-1)).cuda()
+    Y = flat[1:].view(d["Y"].shape)
+    assert Y.data_ptr() % 16 == 8
+    x, L = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "mmse", 16)
+    torch.cuda.synchronize()
+    assert_parity(x.cpu().numpy(), L.cpu().numpy(), d["H"], d["Y"], d["N0"], 1.0, 3,
+                  orc.MMSE, 16)
+
+
+def test_host_entry_point_matches_device_entry_point():
+    d = synth.make_uplink(50, 128, 8, 14, 64, 12.0, 69)
+    Hh = torch.from_numpy(d["H"]).pin_memory()
+    Yh = torch.from_numpy(d["Y"]).pin_memory()
+    xh, Lh = ocd.ocd_detect_host(Hh, Yh, d["N0"], 1.0, 3, "box", 64, pieces=3)
+    xd, Ld = ocd.ocd_detect(Hh.cuda(), Yh.cuda(), d["N0"], 1.0, 3, "box", 64)
+    torch.cuda.synchronize()
+    assert torch.equal(xh, xd.cpu()) and torch.equal(Lh, Ld.cpu())
+
+
+def test_full_size_sampled_against_oracle():
+    """128x8, 64-QAM, K = 3, T = 14 over 1200 x 4 subcarriers in one launch,
+    as the benchmark launches it; sampled subcarriers go to the oracle."""
+    Nsc = 1200 * 4
+    d = synth.make_uplink(Nsc, 128, 8, 14, 64, 15.0, 70)
+    x, L = run_gpu(d, 3, orc.BOX, 64)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(Nsc, 48, replace=False))
+    idx[0], idx[-1] = 0, Nsc - 1
+    assert_parity(x[idx], L[idx], d["H"][idx], d["Y"][idx], d["N0"], 1.0, 3, orc.BOX, 64)
+    assert np.all(np.isfinite(L))
