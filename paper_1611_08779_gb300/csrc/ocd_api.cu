@@ -164,9 +164,10 @@ int validate(const void* H, const void* Y, int Nsc, int B, int U, int T, float N
   if (!alphabet_of(qam_order, al)) return fail(OCD_ERR_ARG, "unsupported qam_order %d", qam_order);
   if (!(Es > 0.0f) || !isfinite(Es)) return fail(OCD_ERR_ARG, "Es must be finite and > 0");
   if (!(N0 >= 0.0f) || !isfinite(N0)) return fail(OCD_ERR_ARG, "N0 must be finite and >= 0");
-  if (!xhat && !llr) return fail(OCD_ERR_ARG, "both outputs are NULL");
   if (llr && !(N0 > 0.0f)) return fail(OCD_ERR_ARG, "LLRs need N0 > 0 (rho~ = ||h||^2 Es/N0)");
+  // An empty problem may come with NULL pointers (empty tensors have no storage).
   const long long items = (long long)Nsc * T;
+  if (items > 0 && !xhat && !llr) return fail(OCD_ERR_ARG, "both outputs are NULL");
   if (items > 0 && (!H || !Y)) return fail(OCD_ERR_ARG, "H and Y must not be NULL");
   if (((uintptr_t)H | (uintptr_t)Y | (uintptr_t)xhat) & 7u)
     return fail(OCD_ERR_ARG, "complex arrays must be 8-byte aligned");

@@ -86,6 +86,7 @@ def test_empty_problem_is_a_no_op(lib):
     # Nsc = 0 or T = 0: nothing to enqueue, OK without a device
     assert call(lib, Nsc=0, H=None, Y=None) == _native.OCD_OK
     assert call(lib, T=0, H=None, Y=None) == _native.OCD_OK
+    assert call(lib, Nsc=0, H=None, Y=None, xhat=None, llr=None) == _native.OCD_OK
 
 
 def test_least_squares_without_llr_is_accepted_by_validation(lib):
