@@ -17,8 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libocd.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ocd_api.cu", "ocd_residual_u4.cu", "ocd_residual_u8.cu",
-           "ocd_residual_u16.cu", "ocd_residual_u32.cu"]
+SOURCES = ["ocd_api.cu", "ocd_residual.cu"]
 
 
 def nvcc_path() -> str:

@@ -11,6 +11,7 @@
 
 #include "ocd.h"
 #include "ocd_common.cuh"
+#include "ocd_residual.cuh"
 
 namespace {
 
@@ -67,15 +68,7 @@ bool alphabet_of(int order, Alphabet& a) {
 // Kernel table: UMAX in {4, 8, 16, 32} x NPP in {2, 4, 8, 16}
 // ---------------------------------------------------------------------------
 using ocd::KernelFn;
-
-KernelFn pick_kernel(int umax, int npp) {
-  switch (umax) {
-    case 4: return ocd::residual_kernel_u4(npp);
-    case 8: return ocd::residual_kernel_u8(npp);
-    case 16: return ocd::residual_kernel_u16(npp);
-    default: return ocd::residual_kernel_u32(npp);
-  }
-}
+constexpr int kNpps[4] = {2, 4, 8, 16};
 
 struct DeviceInfo {
   bool ready = false;
@@ -94,14 +87,11 @@ int device_info(int dev, DeviceInfo& out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    const int umaxes[4] = {4, 8, 16, 32};
-    const int npps[4] = {2, 4, 8, 16};
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) {
-        e = cudaFuncSetAttribute(pick_kernel(umaxes[a], npps[b]),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      }
+    for (int npp : kNpps) {
+      e = cudaFuncSetAttribute(ocd::residual_kernel(npp),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -114,38 +104,30 @@ int device_info(int dev, DeviceInfo& out) {
 // Launch plan
 // ---------------------------------------------------------------------------
 struct Plan {
-  int umax, npp, L, nt;
+  int npp, L, nt;
   size_t smem;
 };
-
-size_t smem_bytes(int scmax, int sc_stride) {
-  return (size_t)scmax * sc_stride * sizeof(float2) + (size_t)scmax * ocd::kUserSlots * 3 * sizeof(float);
-}
 
 // Prefer the fewest lanes per item (fewest shuffles per inner product) whose
 // staged channels fit the shared-memory budget.
 int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl) {
-  pl.umax = U <= 4 ? 4 : U <= 8 ? 8 : U <= 16 ? 16 : 32;
-  const int npp_cap = pl.umax >= 32 ? 8 : 16;
+  const int npp_cap = 16;
   const int pairs = (B + 1) / 2;
   int L = 1;
   while (L * npp_cap < pairs) L <<= 1;
   int nt = 128;
   for (;;) {
-    if (L > 32) return fail(OCD_ERR_UNSUPPORTED, "B=%d U=%d does not fit the team layout", B, U);
+    if (L > 32) return fail(OCD_ERR_UNSUPPORTED, "B=%d does not fit the team layout", B);
     int npp = pow2_ceil((pairs + L - 1) / L);
     if (npp < 2) npp = 2;
     const int teams = nt / L;
     const int chunk = teams;
     int scmax = (chunk - 1 + T - 1) / T + 1;
     if (scmax > chunk) scmax = chunk;
-    const int rs = 2 * L * npp + 2;
-    const int sc_stride = U * rs + 8;
-    const size_t sm = smem_bytes(scmax, sc_stride);
-    if (sm <= budget) {
-      pl.npp = npp; pl.L = L; pl.nt = nt; pl.smem = sm;
+    const ocd::ResidualSmem lay = ocd::residual_smem(L, npp, U, scmax, teams);
+    if (lay.total <= budget) {
+      pl.npp = npp; pl.L = L; pl.nt = nt; pl.smem = lay.total;
       P.L = L; P.logL = ilog2(L); P.chunk = chunk; P.scmax = scmax;
-      P.rs = rs; P.sc_stride = sc_stride;
       return OCD_OK;
     }
     if (L < 32) L <<= 1;
@@ -211,7 +193,7 @@ int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, fl
   if (st != OCD_OK) st = make_plan(B, U, T, di.smem_optin, P, pl);
   if (st != OCD_OK) return st;
 
-  KernelFn fn = pick_kernel(pl.umax, pl.npp);
+  KernelFn fn = ocd::residual_kernel(pl.npp);
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, pl.nt, pl.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");

@@ -32,18 +32,13 @@ struct DetectParams {
   int L, logL;      // lanes per team (power of two) and log2
   int chunk;        // consecutive items per CTA pass (= teams per CTA)
   int scmax;        // largest number of subcarriers a chunk can touch
-  int rs;           // shared-memory row stride of one user column (complex)
-  int sc_stride;    // shared-memory stride between subcarriers (complex)
   int vec_y;        // Y rows may be read with 16-byte loads
 };
 
 using KernelFn = void (*)(DetectParams);
 
-// Kernel tables, one translation unit per user bound (NPP = antenna pairs per lane).
-KernelFn residual_kernel_u4(int npp);
-KernelFn residual_kernel_u8(int npp);
-KernelFn residual_kernel_u16(int npp);
-KernelFn residual_kernel_u32(int npp);
+// Residual-form kernels by antenna pairs per lane (2, 4, 8, 16).
+KernelFn residual_kernel(int npp);
 
 // Projection onto C_O (Eq. 14): for square QAM clip real and imaginary parts
 // independently to [-a, a]; for BPSK clip the real part and zero the

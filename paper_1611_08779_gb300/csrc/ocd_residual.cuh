@@ -1,36 +1,65 @@
 // OCD in the residual form of Algorithm 1, FP32 on the CUDA cores.
 //
 // Work unit ("item"): one (subcarrier w, OFDM symbol t) pair.  A team of L
-// lanes (L a power of two, inside one warp) owns one item: lane l holds the
-// residual entries of antenna pairs {l, l+L, l+2L, ...} (NPP pairs, 2*NPP
-// antennas) in registers for the whole item, so r never leaves the register
-// file between the K sweeps.
+// lanes (L a power of two, inside one warp) owns one item.  Lane l holds the
+// residual entries of the contiguous antenna block [2*NPP*l, 2*NPP*(l+1)) in
+// registers for the whole item, so r never leaves the register file between
+// the K sweeps.
 //
 // A CTA walks over chunks of `chunk` consecutive items (one per team).  The
-// channel columns of every subcarrier the chunk touches are staged once into
-// shared memory, user-major (h_u contiguous, zero-padded to 2*L*NPP antennas),
-// together with the preprocessing of Algorithm 1 (||h_u||^2, d_u^-1, p_u).
-// All T symbols of a subcarrier, and all K sweeps, reuse that copy.
+// channel columns of every subcarrier a chunk touches are staged once into
+// shared memory, user-major, together with the preprocessing of Algorithm 1
+// (||h_u||^2, d_u^-1, p_u); all T symbols and all K sweeps reuse that copy.
+// In a staged column, lane l's block of NPP antenna pairs starts at pair
+// slot l*(NPP+1): the spare slot per block spreads the L lanes of a team
+// over distinct banks, and every load of the sweep is base + immediate.
 //
 // Per (sweep k, user u) a team computes the length-B inner product h_u^H r
 // (lane-partial FMAs, then an xor-butterfly over the L lanes, which leaves a
 // bit-identical sum on every lane), the scalar update with projection
-// (Algorithm 1 update line, Eq. 14) redundantly on every lane, and the rank-1
-// residual update r <- r - h_u dz (Eq. 15 kept incrementally).
+// (Algorithm 1 update line, Eq. 14) on every lane, and the rank-1 residual
+// update r <- r - h_u dz (Eq. 15 kept incrementally).  z lives in shared
+// memory (one slot per user and team) so the user loop stays rolled and the
+// sweep body fits the instruction cache.
 #pragma once
 
 #include "ocd_common.cuh"
 
 namespace ocd {
 
-template <int UMAX, int NPP>
-__global__ void __launch_bounds__(128)
+// Shared-memory layout of the residual kernel (all offsets in bytes).
+struct ResidualSmem {
+  int col_pairs;   // pair slots per staged column: L * (NPP + 1)
+  int rs;          // column stride in complex elements (even)
+  int sc_stride;   // subcarrier stride in complex elements (even)
+  size_t h_bytes, pre_bytes, z_bytes, total;
+};
+
+__host__ __device__ inline ResidualSmem residual_smem(int L, int npp, int U, int scmax, int teams) {
+  ResidualSmem s;
+  s.col_pairs = L * (npp + 1);
+  int rs = 2 * s.col_pairs;
+  // column stride = 4 mod 16 complex: consecutive users land 8 banks apart
+  rs += ((4 - rs) % 16 + 16) % 16;
+  s.rs = rs;
+  s.sc_stride = U * rs + 8;
+  s.h_bytes = (size_t)scmax * s.sc_stride * 8;
+  s.pre_bytes = (size_t)scmax * kUserSlots * 16;  // float2 (d^-1, p) + float ||h||^2 (+pad)
+  s.z_bytes = (size_t)teams * kUserSlots * 8;
+  s.total = s.h_bytes + s.pre_bytes + s.z_bytes;
+  return s;
+}
+
+template <int NPP>
+__global__ void __launch_bounds__(128, 4)
 ocd_residual_kernel(const DetectParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int teams = blockDim.x >> P.logL;
+  const ResidualSmem lay = residual_smem(P.L, NPP, P.U, P.scmax, teams);
   float2* sH = reinterpret_cast<float2*>(smem_raw);
-  float* s_nrm = reinterpret_cast<float*>(sH + (size_t)P.scmax * P.sc_stride);
-  float* s_dinv = s_nrm + P.scmax * kUserSlots;
-  float* s_p = s_dinv + P.scmax * kUserSlots;
+  float2* s_dp = reinterpret_cast<float2*>(smem_raw + lay.h_bytes);            // (d^-1, p)
+  float* s_nrm = reinterpret_cast<float*>(smem_raw + lay.h_bytes) + 2 * P.scmax * kUserSlots;
+  float2* s_z = reinterpret_cast<float2*>(smem_raw + lay.h_bytes + lay.pre_bytes);
 
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
@@ -40,11 +69,21 @@ ocd_residual_kernel(const DetectParams P) {
   const int L = P.L;
   const int lt = tid & (L - 1);
   const int team = tid >> P.logL;
-  const int BU = P.B * P.U;
+  const int U = P.U;
+  const int B = P.B;
 
-  // Antennas B..2*L*NPP-1 of every staged column stay zero for the whole
-  // kernel: the staging loop below only ever writes antennas < B.
-  for (int i = tid; i < P.scmax * P.sc_stride; i += nt) sH[i] = make_float2(0.0f, 0.0f);
+  // Spare slots and antennas >= B stay zero for the whole kernel: staging
+  // below only ever writes the slots of antennas < B.
+  for (int i = tid; i < P.scmax * lay.sc_stride; i += nt) sH[i] = make_float2(0.0f, 0.0f);
+
+  // Staging geometry: a warp copies `rows` antenna rows of U entries at a time
+  // (coalesced), lane -> (row my_r, user my_u); lanes past rows*U idle.
+  const int rows = 32 / U;
+  const int my_r = lane / U;
+  const int my_u = lane - my_r * U;
+  const bool stager = my_r < rows;
+
+  float2* zt = s_z + team * kUserSlots;
 
   const long long nchunks = (P.items + P.chunk - 1) / P.chunk;
   for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -54,27 +93,27 @@ ocd_residual_kernel(const DetectParams P) {
     const int nsc = (int)((i1 - 1) / P.T - sc0 + 1);
 
     __syncthreads();  // the previous chunk is no longer being read
-    // ---- stage H[sc0 .. sc0+nsc) transposed to user-major rows ------------
-    {
-      const float2* gH = P.H + sc0 * (long long)BU;
-      const int tot = nsc * BU;
-      for (int e = tid; e < tot; e += nt) {
-        const int s = e / BU;
-        const int rem = e - s * BU;
-        const int b = rem / P.U;
-        const int u = rem - b * P.U;
-        sH[s * P.sc_stride + u * P.rs + b] = __ldg(gH + e);
+    // ---- stage H[sc0 .. sc0+nsc) as user-major columns -----------------------
+    if (stager) {
+      for (int s = 0; s < nsc; ++s) {
+        const float2* gH = P.H + (sc0 + s) * (long long)B * U;
+        float2* col = sH + s * lay.sc_stride + my_u * lay.rs;
+        for (int b = warp * rows + my_r; b < B; b += nwarps * rows) {
+          const int pp = b >> 1;
+          const int slot = (pp / NPP) * (NPP + 1) + (pp & (NPP - 1));
+          col[2 * slot + (b & 1)] = __ldg(gH + b * U + my_u);
+        }
       }
     }
     __syncthreads();
     // ---- preprocessing (Algorithm 1): ||h_u||^2, d_u^-1, p_u ---------------
-    for (int q = warp; q < nsc * P.U; q += nwarps) {
-      const int s = q / P.U;
-      const int u = q - s * P.U;
-      const float2* row = sH + s * P.sc_stride + u * P.rs;
+    for (int q = warp; q < nsc * U; q += nwarps) {
+      const int s = q / U;
+      const int u = q - s * U;
+      const float2* col = sH + s * lay.sc_stride + u * lay.rs;
       float acc = 0.0f;
-      for (int b = lane; b < P.B; b += 32) {
-        const float2 h = row[b];
+      for (int i = lane; i < 2 * lay.col_pairs; i += 32) {
+        const float2 h = col[i];
         acc = fmaf(h.x, h.x, fmaf(h.y, h.y, acc));
       }
 #pragma unroll
@@ -82,9 +121,8 @@ ocd_residual_kernel(const DetectParams P) {
       if (lane == 0) {
         const float den = acc + P.alpha;
         const float dinv = den > 0.0f ? 1.0f / den : 0.0f;
+        s_dp[s * kUserSlots + u] = make_float2(dinv, dinv * acc);
         s_nrm[s * kUserSlots + u] = acc;
-        s_dinv[s * kUserSlots + u] = dinv;
-        s_p[s * kUserSlots + u] = dinv * acc;
       }
     }
     __syncthreads();
@@ -97,88 +135,87 @@ ocd_residual_kernel(const DetectParams P) {
     // r = y (Algorithm 1 initialization); Y row of item `it` starts at it*B.
     float4 r[NPP];
     {
-      const float2* yrow = P.Y + (active ? it : 0) * (long long)P.B;
+      const float2* yrow = P.Y + (active ? it : 0) * (long long)B;
+      const int p0 = lt * NPP;
 #pragma unroll
       for (int j = 0; j < NPP; ++j) {
-        const int pidx = lt + j * L;
-        const int b0 = 2 * pidx;
+        const int b0 = 2 * (p0 + j);
         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (active) {
           if (P.vec_y) {
-            if (b0 < P.B) v = __ldg(reinterpret_cast<const float4*>(yrow) + pidx);
+            if (b0 < B) v = __ldg(reinterpret_cast<const float4*>(yrow) + p0 + j);
           } else {
-            if (b0 < P.B) { const float2 a = __ldg(yrow + b0); v.x = a.x; v.y = a.y; }
-            if (b0 + 1 < P.B) { const float2 a = __ldg(yrow + b0 + 1); v.z = a.x; v.w = a.y; }
+            if (b0 < B) { const float2 a = __ldg(yrow + b0); v.x = a.x; v.y = a.y; }
+            if (b0 + 1 < B) { const float2 a = __ldg(yrow + b0 + 1); v.z = a.x; v.w = a.y; }
           }
         }
         r[j] = v;
       }
     }
+    for (int u = lt; u < U; u += L) zt[u] = make_float2(0.0f, 0.0f);
+    __syncwarp();
 
-    float2 z[UMAX];
-#pragma unroll
-    for (int u = 0; u < UMAX; ++u) z[u] = make_float2(0.0f, 0.0f);
-
-    const float2* hsc = sH + sl * P.sc_stride;
-    const float* dinv_s = s_dinv + sl * kUserSlots;
-    const float* p_s = s_p + sl * kUserSlots;
+    const float4* hlane = reinterpret_cast<const float4*>(sH + sl * lay.sc_stride) + lt * (NPP + 1);
+    const float2* dp = s_dp + sl * kUserSlots;
+    const int rs4 = lay.rs >> 1;  // column stride in float4
 
     for (int k = 0; k < P.K; ++k) {
+      const bool last_sweep = k == P.K - 1;
+      for (int u = 0; u < U; ++u) {
+        const float4* hc = hlane + u * rs4;
+        const float2 zu = zt[u];
+        const float2 dpu = dp[u];
+        float ar[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float ai[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-      for (int u = 0; u < UMAX; ++u) {
-        if (u < P.U) {
-          const float4* hrow = reinterpret_cast<const float4*>(hsc + u * P.rs);
-          float4 h[NPP];
-          float ar0 = 0.0f, ai0 = 0.0f, ar1 = 0.0f, ai1 = 0.0f;
+        for (int j = 0; j < NPP; ++j) {
+          const float4 h = hc[j];
+          const int a = (j & 1) * 2;
+          // conj(h) * r for the two antennas of the pair
+          ar[a] = fmaf(h.x, r[j].x, ar[a]);
+          ar[a] = fmaf(h.y, r[j].y, ar[a]);
+          ai[a] = fmaf(h.x, r[j].y, ai[a]);
+          ai[a] = fmaf(-h.y, r[j].x, ai[a]);
+          ar[a + 1] = fmaf(h.z, r[j].z, ar[a + 1]);
+          ar[a + 1] = fmaf(h.w, r[j].w, ar[a + 1]);
+          ai[a + 1] = fmaf(h.z, r[j].w, ai[a + 1]);
+          ai[a + 1] = fmaf(-h.w, r[j].z, ai[a + 1]);
+        }
+        float cr = (ar[0] + ar[1]) + (ar[2] + ar[3]);
+        float ci = (ai[0] + ai[1]) + (ai[2] + ai[3]);
+        for (int o = 1; o < L; o <<= 1) {
+          cr += __shfl_xor_sync(kFullMask, cr, o);
+          ci += __shfl_xor_sync(kFullMask, ci, o);
+        }
+        // z_u <- proj(d_u^-1 h_u^H r + p_u z_u); dz = z_new - z_old
+        float wr = fmaf(dpu.x, cr, dpu.y * zu.x);
+        float wi = fmaf(dpu.x, ci, dpu.y * zu.y);
+        project(wr, wi, P);
+        const float dr = wr - zu.x;
+        const float di = wi - zu.y;
+        zt[u] = make_float2(wr, wi);  // every team lane stores the same value
+        // r <- r - h_u dz (not needed after the last update of the last sweep)
+        if (!(last_sweep && u == U - 1)) {
 #pragma unroll
           for (int j = 0; j < NPP; ++j) {
-            h[j] = hrow[lt + j * L];
-            // conj(h) * r for the two antennas of the pair
-            ar0 = fmaf(h[j].x, r[j].x, ar0);
-            ar0 = fmaf(h[j].y, r[j].y, ar0);
-            ai0 = fmaf(h[j].x, r[j].y, ai0);
-            ai0 = fmaf(-h[j].y, r[j].x, ai0);
-            ar1 = fmaf(h[j].z, r[j].z, ar1);
-            ar1 = fmaf(h[j].w, r[j].w, ar1);
-            ai1 = fmaf(h[j].z, r[j].w, ai1);
-            ai1 = fmaf(-h[j].w, r[j].z, ai1);
-          }
-          float cr = ar0 + ar1;
-          float ci = ai0 + ai1;
-          for (int o = 1; o < L; o <<= 1) {
-            cr += __shfl_xor_sync(kFullMask, cr, o);
-            ci += __shfl_xor_sync(kFullMask, ci, o);
-          }
-          // z_u <- proj(d_u^-1 h_u^H r + p_u z_u); dz = z_new - z_old
-          const float dv = dinv_s[u];
-          const float pv = p_s[u];
-          float wr = fmaf(dv, cr, pv * z[u].x);
-          float wi = fmaf(dv, ci, pv * z[u].y);
-          project(wr, wi, P);
-          const float dr = wr - z[u].x;
-          const float di = wi - z[u].y;
-          z[u] = make_float2(wr, wi);
-          // r <- r - h_u dz
-#pragma unroll
-          for (int j = 0; j < NPP; ++j) {
-            r[j].x = fmaf(-h[j].x, dr, fmaf(h[j].y, di, r[j].x));
-            r[j].y = fmaf(-h[j].x, di, fmaf(-h[j].y, dr, r[j].y));
-            r[j].z = fmaf(-h[j].z, dr, fmaf(h[j].w, di, r[j].z));
-            r[j].w = fmaf(-h[j].z, di, fmaf(-h[j].w, dr, r[j].w));
+            const float4 h = hc[j];
+            r[j].x = fmaf(-h.x, dr, fmaf(h.y, di, r[j].x));
+            r[j].y = fmaf(-h.x, di, fmaf(-h.y, dr, r[j].y));
+            r[j].z = fmaf(-h.z, dr, fmaf(h.w, di, r[j].z));
+            r[j].w = fmaf(-h.z, di, fmaf(-h.w, dr, r[j].w));
           }
         }
       }
     }
+    __syncwarp();
 
     // ---- outputs: users are spread over the team's lanes -------------------
     if (active) {
-      const float* nrm_s = s_nrm + sl * kUserSlots;
-#pragma unroll
-      for (int u = 0; u < UMAX; ++u) {
-        if (u < P.U && (u & (L - 1)) == lt) {
-          if (P.xhat) P.xhat[it * P.U + u] = z[u];
-          if (P.llr) user_llr(z[u], nrm_s[u], p_s[u], P, P.llr + (it * P.U + u) * P.Q);
-        }
+      const float* nrm = s_nrm + sl * kUserSlots;
+      for (int u = lt; u < U; u += L) {
+        const float2 z = zt[u];
+        if (P.xhat) P.xhat[it * U + u] = z;
+        if (P.llr) user_llr(z, nrm[u], dp[u].y, P, P.llr + (it * U + u) * P.Q);
       }
     }
   }
