@@ -87,11 +87,12 @@ int device_info(int dev, DeviceInfo& out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    for (int npp : kNpps) {
-      e = cudaFuncSetAttribute(ocd::residual_kernel(npp),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    }
+    for (int S = 1; S <= 2; ++S)
+      for (int npp : kNpps) {
+        e = cudaFuncSetAttribute(ocd::residual_kernel(npp, S),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -104,14 +105,17 @@ int device_info(int dev, DeviceInfo& out) {
 // Launch plan
 // ---------------------------------------------------------------------------
 struct Plan {
-  int npp, L, nt;
+  int npp, S, L, nt;
   size_t smem;
 };
 
-// Prefer the fewest lanes per item (fewest shuffles per inner product) whose
-// staged channels fit the shared-memory budget.
+// Two symbols per item when a subcarrier carries several (each staged h
+// block then feeds two inner products and two residual updates); the fewest
+// lanes per item (fewest shuffles) whose staged channels fit the budget.
 int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl) {
-  const int npp_cap = 16;
+  const int S = T >= 2 ? 2 : 1;
+  const int G = (T + S - 1) / S;
+  const int npp_cap = 8;
   const int pairs = (B + 1) / 2;
   int L = 1;
   while (L * npp_cap < pairs) L <<= 1;
@@ -122,12 +126,13 @@ int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl
     if (npp < 2) npp = 2;
     const int teams = nt / L;
     const int chunk = teams;
-    int scmax = (chunk - 1 + T - 1) / T + 1;
+    int scmax = (chunk - 1 + G - 1) / G + 1;
     if (scmax > chunk) scmax = chunk;
-    const ocd::ResidualSmem lay = ocd::residual_smem(L, npp, U, scmax, teams);
+    const ocd::ResidualSmem lay = ocd::residual_smem(L, npp, S, U, scmax, teams);
     if (lay.total <= budget) {
-      pl.npp = npp; pl.L = L; pl.nt = nt; pl.smem = lay.total;
+      pl.npp = npp; pl.S = S; pl.L = L; pl.nt = nt; pl.smem = lay.total;
       P.L = L; P.logL = ilog2(L); P.chunk = chunk; P.scmax = scmax;
+      P.items = (long long)P.Nsc * G;
       return OCD_OK;
     }
     if (L < 32) L <<= 1;
@@ -193,12 +198,12 @@ int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, fl
   if (st != OCD_OK) st = make_plan(B, U, T, di.smem_optin, P, pl);
   if (st != OCD_OK) return st;
 
-  KernelFn fn = ocd::residual_kernel(pl.npp);
+  KernelFn fn = ocd::residual_kernel(pl.npp, pl.S);
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, pl.nt, pl.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (per_sm < 1) return fail(OCD_ERR_UNSUPPORTED, "kernel cannot be resident (smem %zu)", pl.smem);
-  const long long nchunks = (items + P.chunk - 1) / P.chunk;
+  const long long nchunks = (P.items + P.chunk - 1) / P.chunk;
   long long grid = (long long)di.sms * per_sm;
   if (grid > nchunks) grid = nchunks;
   void* args[] = {&P};

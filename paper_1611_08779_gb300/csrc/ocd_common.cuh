@@ -16,7 +16,7 @@ struct DetectParams {
   const float2* __restrict__ Y;  // [Nsc][T][B]
   float2* __restrict__ xhat;     // [Nsc][T][U] or null
   float* __restrict__ llr;       // [Nsc][T][U][Q] or null
-  long long items;               // Nsc * T (one item = one subcarrier-symbol pair)
+  long long items;               // Nsc * ceil(T / S) (one item = S symbols of one subcarrier)
   int Nsc, B, U, T, K;
   int box;        // 1: BOX mode (clip), 0: MMSE mode
   int bpsk;       // 1: BPSK alphabet (real axis only)
@@ -37,8 +37,9 @@ struct DetectParams {
 
 using KernelFn = void (*)(DetectParams);
 
-// Residual-form kernels by antenna pairs per lane (2, 4, 8, 16).
-KernelFn residual_kernel(int npp);
+// Residual-form kernels by antenna pairs per lane (2, 4, 8, 16) and symbols
+// per item (1, 2).
+KernelFn residual_kernel(int npp, int s);
 
 // Projection onto C_O (Eq. 14): for square QAM clip real and imaginary parts
 // independently to [-a, a]; for BPSK clip the real part and zero the
@@ -50,30 +51,41 @@ __device__ __forceinline__ void project(float& wr, float& wi, const DetectParams
   }
 }
 
-// Max-log LLRs (Eq. 9) of the bits carried by one real dimension.  For a
-// separable Gray alphabet the minima over O_b^0 and O_b^1 differ only in this
-// dimension, so the other dimension's contribution cancels exactly.
-__device__ __forceinline__ void dimension_llr(float x, float rho, const DetectParams& P,
-                                              float* out) {
-  float d0[4], d1[4];
+// Max-log LLRs (Eq. 9) of the bits carried by one real dimension with NB
+// bits (M = 2^NB levels).  For a separable Gray alphabet the minima over
+// O_b^0 and O_b^1 differ only in this dimension, so the other dimension's
+// contribution cancels exactly.  Level i sits at (2i + 1 - M) * step and
+// carries the Gray word i ^ (i >> 1); the loops unroll completely, so every
+// label test is resolved at compile time.
+template <int NB>
+__device__ __forceinline__ void dimension_llr_nb(float x, float rho, float step, float* out) {
+  constexpr int M = 1 << NB;
+  float d0[NB], d1[NB];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) { d0[j] = FLT_MAX; d1[j] = FLT_MAX; }
-  for (int i = 0; i < P.M; ++i) {
-    const float a = (float)(2 * i + 1 - P.M) * P.lvl_step;
-    const float e = x - a;
+  for (int j = 0; j < NB; ++j) { d0[j] = FLT_MAX; d1[j] = FLT_MAX; }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float e = x - (float)(2 * i + 1 - M) * step;
     const float d = e * e;
-    const int g = i ^ (i >> 1);  // Gray word of level i
+    const int g = i ^ (i >> 1);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (j < P.nb) {
-        if ((g >> (P.nb - 1 - j)) & 1) d1[j] = fminf(d1[j], d);
-        else d0[j] = fminf(d0[j], d);
-      }
+    for (int j = 0; j < NB; ++j) {
+      if ((g >> (NB - 1 - j)) & 1) d1[j] = fminf(d1[j], d);
+      else d0[j] = fminf(d0[j], d);
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (j < P.nb) out[j] = rho * (d0[j] - d1[j]);
+  for (int j = 0; j < NB; ++j) out[j] = rho * (d0[j] - d1[j]);
+}
+
+__device__ __forceinline__ void dimension_llr(float x, float rho, const DetectParams& P,
+                                              float* out) {
+  switch (P.nb) {
+    case 1: dimension_llr_nb<1>(x, rho, P.lvl_step, out); break;
+    case 2: dimension_llr_nb<2>(x, rho, P.lvl_step, out); break;
+    case 3: dimension_llr_nb<3>(x, rho, P.lvl_step, out); break;
+    default: dimension_llr_nb<4>(x, rho, P.lvl_step, out); break;
+  }
 }
 
 // Soft output of one user (Section III-C): mu~ = p, rho~ = ||h||^2 Es / N0,
