@@ -47,6 +47,19 @@ extern "C" {
 
 typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
 
+/*
+ * Two arrangements of the same Algorithm 1 arithmetic (identical iterates in
+ * exact arithmetic; both checked against the same FP64 reference):
+ *   OCD_ALGO_RESIDUAL   r = y - sum_j h_j z_j kept in full (B entries per
+ *                       symbol): 8B real FMAs per user update, as written.
+ *   OCD_ALGO_PROJECTED  r carried as q = H^H r (U entries per symbol):
+ *                       q0 = H^H y and G = H^H H once per subcarrier, then
+ *                       h_u^H r = q_u and r -= h_u dz becomes q -= G[:,u] dz.
+ *                       Supports U <= 8.
+ *   OCD_ALGO_AUTO       PROJECTED when U <= 8 and T >= 2, else RESIDUAL.
+ */
+typedef enum { OCD_ALGO_AUTO = 0, OCD_ALGO_RESIDUAL = 1, OCD_ALGO_PROJECTED = 2 } ocd_algo_t;
+
 typedef enum {
   OCD_OK = 0,
   OCD_ERR_ARG = -1,          /* invalid argument; nothing was enqueued          */
@@ -61,7 +74,8 @@ typedef enum {
 
 /*
  * ocd_detect -- Algorithm 1 (preprocessing, K sweeps of h_u^H r, scalar
- * update with projection, residual update r -= h_u dz) followed by Eq. 9.
+ * update with projection, residual update r -= h_u dz) followed by Eq. 9,
+ * in the arrangement OCD_ALGO_AUTO picks.
  *
  *   H, Y        device pointers, layouts above.  Must not be NULL when
  *               Nsc*T > 0.  8-byte alignment is required; 16-byte alignment
@@ -80,6 +94,15 @@ typedef enum {
 int ocd_detect(const void* H, const void* Y, int Nsc, int B, int U, int T,
                float N0, float Es, int K, int mode, int qam_order,
                void* xhat, float* llr, cudaStream_t stream);
+
+/*
+ * ocd_detect_ex -- ocd_detect with an explicit arrangement `algo`
+ * (ocd_algo_t).  ocd_detect(...) is ocd_detect_ex(..., OCD_ALGO_AUTO, stream).
+ * OCD_ALGO_PROJECTED with U > 8 returns OCD_ERR_UNSUPPORTED.
+ */
+int ocd_detect_ex(const void* H, const void* Y, int Nsc, int B, int U, int T,
+                  float N0, float Es, int K, int mode, int qam_order,
+                  void* xhat, float* llr, int algo, cudaStream_t stream);
 
 /*
  * ocd_detect_host -- the same computation on HOST buffers (Eq. 1 inputs in,

@@ -17,6 +17,10 @@ MODES = {"mmse": _native.OCD_MMSE, "box": _native.OCD_BOX,
          _native.OCD_MMSE: _native.OCD_MMSE, _native.OCD_BOX: _native.OCD_BOX}
 
 
+ALGOS = {"auto": _native.OCD_ALGO_AUTO, "residual": _native.OCD_ALGO_RESIDUAL,
+         "projected": _native.OCD_ALGO_PROJECTED}
+
+
 def bits_per_symbol(qam_order: int) -> int:
     if qam_order not in (2, 4, 16, 64, 256):
         raise ValueError(f"unsupported qam_order {qam_order}")
@@ -50,11 +54,13 @@ def _stream_handle(stream) -> int:
 def ocd_detect(H: torch.Tensor, Y: torch.Tensor, N0: float, Es: float = 1.0, K: int = 3,
                mode="mmse", qam_order: int = 64, xhat: torch.Tensor | None = None,
                llr: torch.Tensor | None = None, want_xhat: bool = True, want_llr: bool = True,
-               stream: torch.cuda.Stream | None = None):
+               algo: str = "auto", stream: torch.cuda.Stream | None = None):
     """OCD equalization (Algorithm 1) and max-log LLRs (Eq. 9) on the GPU.
 
     H: complex64 [Nsc, B, U] and Y: complex64 [Nsc, T, B] on one CUDA device.
-    Returns (xhat complex64 [Nsc, T, U] or None, llr float32 [Nsc, T, U, Q] or None).
+    `algo` picks the arrangement ("auto", "residual" or "projected"; see
+    include/ocd.h).  Returns (xhat complex64 [Nsc, T, U] or None,
+    llr float32 [Nsc, T, U, Q] or None).
     The work is enqueued on `stream` (default: the current stream); nothing
     is synchronized.
     """
@@ -84,12 +90,14 @@ def ocd_detect(H: torch.Tensor, Y: torch.Tensor, N0: float, Es: float = 1.0, K: 
             raise ValueError("llr must be a contiguous float32 tensor on H's device")
         if tuple(llr.shape) != (Nsc, T, U, Q):
             raise ValueError("llr must be [Nsc, T, U, Q]")
+    if algo not in ALGOS:
+        raise ValueError(f"unknown algo {algo!r}")
     with torch.cuda.device(dev):
-        st = lib.ocd_detect(H.data_ptr(), Y.data_ptr(), Nsc, B, U, T, float(N0), float(Es),
-                            int(K), _mode(mode), int(qam_order),
-                            xhat.data_ptr() if xhat is not None else None,
-                            llr.data_ptr() if llr is not None else None,
-                            _stream_handle(stream))
+        st = lib.ocd_detect_ex(H.data_ptr(), Y.data_ptr(), Nsc, B, U, T, float(N0), float(Es),
+                               int(K), _mode(mode), int(qam_order),
+                               xhat.data_ptr() if xhat is not None else None,
+                               llr.data_ptr() if llr is not None else None,
+                               ALGOS[algo], _stream_handle(stream))
     _native.check(st)
     return xhat, llr
 

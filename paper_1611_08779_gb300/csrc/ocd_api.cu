@@ -93,6 +93,11 @@ int device_info(int dev, DeviceInfo& out) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
       }
+    for (int umax : {4, 8}) {
+      e = cudaFuncSetAttribute(ocd::projected_kernel(umax),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -142,7 +147,10 @@ int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl
 }
 
 int validate(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
-             int K, int mode, int qam_order, const void* xhat, const void* llr, Alphabet& al) {
+             int K, int mode, int qam_order, const void* xhat, const void* llr, int algo,
+             Alphabet& al) {
+  if (algo != OCD_ALGO_AUTO && algo != OCD_ALGO_RESIDUAL && algo != OCD_ALGO_PROJECTED)
+    return fail(OCD_ERR_ARG, "unknown algo %d", algo);
   if (Nsc < 0 || T < 0) return fail(OCD_ERR_ARG, "Nsc=%d and T=%d must be >= 0", Nsc, T);
   if (B < 1 || B > OCD_MAX_ANTENNAS) return fail(OCD_ERR_ARG, "B=%d outside 1..%d", B, OCD_MAX_ANTENNAS);
   if (U < 1 || U > OCD_MAX_USERS) return fail(OCD_ERR_ARG, "U=%d outside 1..%d", U, OCD_MAX_USERS);
@@ -162,8 +170,36 @@ int validate(const void* H, const void* Y, int Nsc, int B, int U, int T, float N
   return OCD_OK;
 }
 
+// Algorithm choice for OCD_ALGO_AUTO: the projected form wins whenever its
+// two per-subcarrier products are shared by more than one symbol.
+int resolve_algo(int algo, int U, int T) {
+  if (algo != OCD_ALGO_AUTO) return algo;
+  return (U <= ocd::kProjectedMaxUsers && T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+}
+
+int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
+  const int umax = U <= 4 ? 4 : 8;
+  KernelFn fn = ocd::projected_kernel(umax);
+  const int nt = 128;
+  const size_t smem = (nt / 32) * ocd::projected_smem_per_warp(umax);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (per_sm < 1) return fail(OCD_ERR_UNSUPPORTED, "projected kernel cannot be resident");
+  const long long warps_needed = P.Nsc;
+  long long grid = (long long)di.sms * per_sm;
+  const long long need = (warps_needed + nt / 32 - 1) / (nt / 32);
+  if (grid > need) grid = need;
+  void* args[] = {&P};
+  e = cudaLaunchKernel((const void*)fn, dim3((unsigned)grid), dim3(nt), args, smem, stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return OCD_OK;
+}
+
 int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
-                  int K, int mode, const Alphabet& al, void* xhat, float* llr, cudaStream_t stream) {
+                  int K, int mode, const Alphabet& al, void* xhat, float* llr, int algo,
+                  cudaStream_t stream) {
   const long long items = (long long)Nsc * T;
   if (items == 0) return OCD_OK;
   ocd::DetectParams P;
@@ -190,6 +226,14 @@ int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, fl
   DeviceInfo di;
   int st = device_info(dev, di);
   if (st != OCD_OK) return st;
+
+  algo = resolve_algo(algo, U, T);
+  if (algo == OCD_ALGO_PROJECTED) {
+    if (U > ocd::kProjectedMaxUsers)
+      return fail(OCD_ERR_UNSUPPORTED, "projected form supports U <= %d (got %d)",
+                  ocd::kProjectedMaxUsers, U);
+    return launch_projected(P, di, U, stream);
+  }
 
   // Keep several CTAs per SM when the staged channels allow it; otherwise
   // take up to the whole opt-in shared memory of one CTA.
@@ -246,19 +290,26 @@ int host_streams(int dev, HostStreams*& out) {
 
 extern "C" {
 
+int ocd_detect_ex(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
+                  int K, int mode, int qam_order, void* xhat, float* llr, int algo,
+                  cudaStream_t stream) {
+  Alphabet al;
+  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, algo, al);
+  if (st != OCD_OK) return st;
+  return launch_detect(H, Y, Nsc, B, U, T, N0, Es, K, mode, al, xhat, llr, algo, stream);
+}
+
 int ocd_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
                int K, int mode, int qam_order, void* xhat, float* llr, cudaStream_t stream) {
-  Alphabet al;
-  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, al);
-  if (st != OCD_OK) return st;
-  return launch_detect(H, Y, Nsc, B, U, T, N0, Es, K, mode, al, xhat, llr, stream);
+  return ocd_detect_ex(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, OCD_ALGO_AUTO,
+                       stream);
 }
 
 int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
                     int K, int mode, int qam_order, void* xhat, float* llr, void* dH, void* dY,
                     void* dX, float* dL, int pieces, cudaStream_t stream) {
   Alphabet al;
-  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, al);
+  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, OCD_ALGO_AUTO, al);
   if (st != OCD_OK) return st;
   if (pieces < 1 || pieces > 64) return fail(OCD_ERR_ARG, "pieces=%d outside 1..64", pieces);
   const long long items = (long long)Nsc * T;
@@ -304,7 +355,7 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync Y");
     char* dx = xhat ? static_cast<char*>(dX) + a * xsz : nullptr;
     float* dl = llr ? reinterpret_cast<float*>(reinterpret_cast<char*>(dL) + a * lsz) : nullptr;
-    st = launch_detect(dh, dy, n, B, U, T, N0, Es, K, mode, al, dx, dl, s);
+    st = launch_detect(dh, dy, n, B, U, T, N0, Es, K, mode, al, dx, dl, OCD_ALGO_AUTO, s);
     if (st != OCD_OK) return st;
     if (xhat) {
       e = cudaMemcpyAsync(static_cast<char*>(xhat) + a * xsz, dx, n * xsz, cudaMemcpyDeviceToHost, s);

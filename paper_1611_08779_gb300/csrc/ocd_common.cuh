@@ -40,6 +40,11 @@ using KernelFn = void (*)(DetectParams);
 // Residual-form kernels by antenna pairs per lane (2, 4, 8, 16) and symbols
 // per item (1, 2).
 KernelFn residual_kernel(int npp, int s);
+// Projected-residual kernels by user bound (4 or 8) and their per-warp
+// shared memory in bytes.
+KernelFn projected_kernel(int umax);
+size_t projected_smem_per_warp(int umax);
+constexpr int kProjectedMaxUsers = 8;
 
 // Projection onto C_O (Eq. 14): for square QAM clip real and imaginary parts
 // independently to [-a, a]; for BPSK clip the real part and zero the

@@ -16,22 +16,32 @@ from .parity import assert_parity, xhat_error  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 MODE = {orc.MMSE: "mmse", orc.BOX: "box"}
+ALGOS = ["residual", "projected"]
 
 
-def run_gpu(d, K, mode, order, Es=1.0, N0=None, want_xhat=True, want_llr=True):
+def algos_for(U):
+    return ALGOS if U <= 8 else ["residual"]
+
+
+def run_gpu(d, K, mode, order, Es=1.0, N0=None, want_xhat=True, want_llr=True, algo="auto"):
     H = torch.from_numpy(d["H"]).cuda()
     Y = torch.from_numpy(d["Y"]).cuda()
     x, L = ocd.ocd_detect(H, Y, d["N0"] if N0 is None else N0, Es, K, MODE[mode], order,
-                          want_xhat=want_xhat, want_llr=want_llr)
+                          want_xhat=want_xhat, want_llr=want_llr, algo=algo)
     torch.cuda.synchronize()
     return (x.cpu().numpy() if x is not None else None,
             L.cpu().numpy() if L is not None else None)
 
 
-def check(Nsc, B, U, T, K, mode, order, snr, seed, Es=1.0, label=""):
+def check(Nsc, B, U, T, K, mode, order, snr, seed, Es=1.0, label="", algos=None):
+    """Every arrangement that supports the shape must match the oracle."""
     d = synth.make_uplink(Nsc, B, U, T, order, snr, seed, Es=Es)
-    x, L = run_gpu(d, K, mode, order, Es)
-    return assert_parity(x, L, d["H"], d["Y"], d["N0"], Es, K, mode, order, label)
+    out = {}
+    for algo in (algos or algos_for(U)):
+        x, L = run_gpu(d, K, mode, order, Es, algo=algo)
+        out[algo] = assert_parity(x, L, d["H"], d["Y"], d["N0"], Es, K, mode, order,
+                                  f"{label} [{algo}]")
+    return out
 
 
 # Small configuration of the paper's 32x8 system: 64 subcarriers, T = 1, K = 3,
@@ -80,29 +90,32 @@ def test_symbol_energy_not_one():
     check(8, 64, 8, 6, 3, orc.BOX, 16, 12.0, 62, Es=0.3)
 
 
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
-def test_zero_column(mode):
+def test_zero_column(mode, algo):
     d = synth.make_uplink(6, 32, 5, 3, 16, 10.0, 63)
     d["H"][:, :, 3] = 0
     d["H"][2, :, 0] = 0
-    x, L = run_gpu(d, 3, mode, 16)
+    x, L = run_gpu(d, 3, mode, 16, algo=algo)
     assert np.all(x[:, :, 3] == 0) and np.all(L[:, :, 3] == 0)
     assert_parity(x, L, d["H"], d["Y"], d["N0"], 1.0, 3, mode, 16)
 
 
-def test_least_squares_mmse_with_zero_noise():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_least_squares_mmse_with_zero_noise(algo):
     d = synth.make_uplink(5, 64, 8, 3, 64, 20.0, 64)
-    x, L = run_gpu(d, 6, orc.MMSE, 64, N0=0.0, want_llr=False)
+    x, L = run_gpu(d, 6, orc.MMSE, 64, N0=0.0, want_llr=False, algo=algo)
     assert L is None
     z_ref, *_ = orc.ocd_equalize(d["H"], d["Y"], 0.0, 1.0, 6, orc.MMSE, 64)
     assert xhat_error(x, z_ref) <= 1e-4
 
 
-def test_outputs_optional():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_outputs_optional(algo):
     d = synth.make_uplink(5, 32, 4, 3, 16, 10.0, 65)
-    x1, L1 = run_gpu(d, 3, orc.BOX, 16)
-    x2, L2 = run_gpu(d, 3, orc.BOX, 16, want_llr=False)
-    x3, L3 = run_gpu(d, 3, orc.BOX, 16, want_xhat=False)
+    x1, L1 = run_gpu(d, 3, orc.BOX, 16, algo=algo)
+    x2, L2 = run_gpu(d, 3, orc.BOX, 16, want_llr=False, algo=algo)
+    x3, L3 = run_gpu(d, 3, orc.BOX, 16, want_xhat=False, algo=algo)
     assert L2 is None and x3 is None
     assert np.array_equal(x1, x2) and np.array_equal(L1, L3)
 
@@ -119,28 +132,31 @@ def test_empty_inputs():
     assert x.shape == (4, 0, 4)
 
 
-def test_noiseless_recovery_on_gpu():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_noiseless_recovery_on_gpu(algo):
     d = synth.make_noiseless(16, 128, 8, 14, 64, seed=66)
     d["H"] = d["H"].astype(np.complex64)
     d["Y"] = d["Y"].astype(np.complex64)
     d["N0"] = 1e-6
-    x, L = run_gpu(d, 8, orc.BOX, 64)
+    x, L = run_gpu(d, 8, orc.BOX, 64, algo=algo)
     assert np.array_equal((L > 0).astype(np.uint8), d["bits"])
 
 
-def test_deterministic_and_stream_independent():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_deterministic_and_stream_independent(algo):
     d = synth.make_uplink(40, 128, 8, 14, 64, 15.0, 67)
     H = torch.from_numpy(d["H"]).cuda()
     Y = torch.from_numpy(d["Y"]).cuda()
-    x1, L1 = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "box", 64)
+    x1, L1 = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "box", 64, algo=algo)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        x2, L2 = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "box", 64)
+        x2, L2 = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "box", 64, algo=algo)
     torch.cuda.synchronize()
     assert torch.equal(x1, x2) and torch.equal(L1, L2)
 
 
-def test_unaligned_y_uses_scalar_loads():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_unaligned_y_uses_scalar_loads(algo):
     # Y starting 8 bytes past a 16-byte boundary takes the scalar-load path
     d = synth.make_uplink(6, 64, 8, 3, 16, 10.0, 68)
     H = torch.from_numpy(d["H"]).cuda()
@@ -148,7 +164,7 @@ def test_unaligned_y_uses_scalar_loads():
     flat[1:] = torch.from_numpy(d["Y"].reshape(-1)).cuda()
     Y = flat[1:].view(d["Y"].shape)
     assert Y.data_ptr() % 16 == 8
-    x, L = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "mmse", 16)
+    x, L = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, "mmse", 16, algo=algo)
     torch.cuda.synchronize()
     assert_parity(x.cpu().numpy(), L.cpu().numpy(), d["H"], d["Y"], d["N0"], 1.0, 3,
                   orc.MMSE, 16)
@@ -164,14 +180,32 @@ def test_host_entry_point_matches_device_entry_point():
     assert torch.equal(xh, xd.cpu()) and torch.equal(Lh, Ld.cpu())
 
 
-def test_full_size_sampled_against_oracle():
+@pytest.mark.parametrize("algo", ["auto", "residual", "projected"])
+def test_full_size_sampled_against_oracle(algo):
     """128x8, 64-QAM, K = 3, T = 14 over 1200 x 4 subcarriers in one launch,
     as the benchmark launches it; sampled subcarriers go to the oracle."""
     Nsc = 1200 * 4
     d = synth.make_uplink(Nsc, 128, 8, 14, 64, 15.0, 70)
-    x, L = run_gpu(d, 3, orc.BOX, 64)
+    x, L = run_gpu(d, 3, orc.BOX, 64, algo=algo)
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(Nsc, 48, replace=False))
     idx[0], idx[-1] = 0, Nsc - 1
     assert_parity(x[idx], L[idx], d["H"][idx], d["Y"][idx], d["N0"], 1.0, 3, orc.BOX, 64)
     assert np.all(np.isfinite(L))
+
+
+def test_projected_rejects_more_than_eight_users():
+    d = synth.make_uplink(2, 32, 9, 2, 16, 10.0, 71)
+    with pytest.raises(ocd.OcdError, match="UNSUPPORTED"):
+        run_gpu(d, 3, orc.MMSE, 16, algo="projected")
+    x, L = run_gpu(d, 3, orc.MMSE, 16, algo="auto")  # falls back to the residual form
+    assert_parity(x, L, d["H"], d["Y"], d["N0"], 1.0, 3, orc.MMSE, 16)
+
+
+@pytest.mark.parametrize("T", [1, 2, 15, 16, 17, 33, 40])
+@pytest.mark.parametrize("U", [1, 3, 4, 5, 8])
+def test_projected_symbol_passes_and_user_bounds(U, T):
+    """Symbol counts around the per-pass width (16 symbols for U <= 8, 32 for
+    U <= 4) and user counts around both instance bounds."""
+    check(5, 40, U, T, 3, orc.BOX, 16, 8.0, 100 * U + T, label=f"U{U} T{T}",
+          algos=["projected"])
