@@ -122,6 +122,14 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T,
                     void* dH, void* dY, void* dX, float* dL,
                     int pieces, cudaStream_t stream);
 
+/*
+ * ocd_fault_status -- fault word of the kernels that wait on copy engines
+ * (bit 0: a bounded wait for a bulk copy expired; the affected subcarriers
+ * were left unwritten).  Returns the bits (>= 0) or OCD_ERR_CUDA, and clears
+ * them when `clear` is non-zero.  Synchronizes with the current device.
+ */
+int ocd_fault_status(int clear);
+
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* ocd_last_error(void);
 

@@ -5,5 +5,6 @@ runs in the CUDA library libocd.so; this package is its Python binding plus
 the seeded input generator and the subcarrier partition used by the benchmark.
 """
 from ._native import OcdError  # noqa: F401
-from .api import bits_per_symbol, make_staging, ocd_detect, ocd_detect_host, version  # noqa: F401
+from .api import (bits_per_symbol, fault_status, make_staging, ocd_detect,  # noqa: F401
+                  ocd_detect_host, version)
 from .shard import shard_range  # noqa: F401

@@ -152,5 +152,13 @@ def make_staging(Nsc: int, B: int, U: int, T: int, qam_order: int, device) -> di
     }
 
 
+def fault_status(clear: bool = True) -> int:
+    """Fault bits of the bulk-copy kernels (0 = no wait expired); synchronizes."""
+    st = _native.load().ocd_fault_status(1 if clear else 0)
+    if st < 0:
+        _native.check(st)
+    return st
+
+
 def version() -> int:
     return _native.load().ocd_version()

@@ -97,6 +97,9 @@ int device_info(int dev, DeviceInfo& out) {
       e = cudaFuncSetAttribute(ocd::projected_kernel(umax),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      e = cudaFuncSetAttribute(ocd::projected_tma_kernel(umax),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
@@ -177,11 +180,20 @@ int resolve_algo(int algo, int U, int T) {
   return (U <= ocd::kProjectedMaxUsers && T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
 }
 
+// The bulk-copy variant streams H and Y through shared memory; it needs
+// 16-byte aligned rows, i.e. even B and 16-byte aligned bases.
+bool tma_eligible(const ocd::DetectParams& P) {
+  return (P.B % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.H) & 15u) == 0) &&
+         ((reinterpret_cast<uintptr_t>(P.Y) & 15u) == 0);
+}
+
 int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
   const int umax = U <= 4 ? 4 : 8;
-  KernelFn fn = ocd::projected_kernel(umax);
+  const bool tma = tma_eligible(P);
+  KernelFn fn = tma ? ocd::projected_tma_kernel(umax) : ocd::projected_kernel(umax);
   const int nt = 128;
-  const size_t smem = (nt / 32) * ocd::projected_smem_per_warp(umax);
+  const size_t smem = (nt / 32) * (tma ? ocd::projected_tma_smem_per_warp(umax)
+                                       : ocd::projected_smem_per_warp(umax));
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
@@ -373,6 +385,13 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
   }
   return OCD_OK;
+}
+
+int ocd_fault_status(int clear) {
+  unsigned int bits = 0;
+  cudaError_t e = ocd::projected_tma_fault(&bits, clear != 0);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the fault word");
+  return (int)bits;
 }
 
 const char* ocd_last_error(void) { return g_err; }

@@ -45,6 +45,12 @@ KernelFn residual_kernel(int npp, int s);
 KernelFn projected_kernel(int umax);
 size_t projected_smem_per_warp(int umax);
 constexpr int kProjectedMaxUsers = 8;
+// Bulk-copy (TMA) projected kernels: needs even B and 16-byte aligned H, Y.
+KernelFn projected_tma_kernel(int umax);
+size_t projected_tma_smem_per_warp(int umax);
+// Reads (and optionally clears) the fault word of the bulk-copy kernels;
+// synchronous with respect to the device.
+cudaError_t projected_tma_fault(unsigned int* bits, bool clear);
 
 // Projection onto C_O (Eq. 14): for square QAM clip real and imaginary parts
 // independently to [-a, a]; for BPSK clip the real part and zero the

@@ -17,8 +17,9 @@
 //     accumulates q0 for the symbols c, c+4, c+8, ... of the current symbol
 //     pass (TS = 32/UMAX of them) and the columns c, c+4, ... of G (both
 //     triangles, so every lane runs the same code).  H rows and Y pairs are
-//     read with vector loads; the subcarrier two steps ahead is prefetched
-//     into L2 with a bulk prefetch.
+//     read with vector loads straight from global memory (this variant
+//     serves shapes the bulk-copy variant cannot stage: odd B, unaligned
+//     bases).
 //   Reduction: the eight antenna-group partials are summed through shared
 //     memory (fixed order, g = 0..7).
 //   Sweeps: one lane per symbol runs the K round-robin sweeps on q with z in
@@ -48,28 +49,6 @@ struct ProjectedShape {
   static constexpr int kWarpFloats = kRed + kQ + kG + kZ + kPre;
 };
 
-__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
-  // TMA bulk prefetch of a contiguous, 16-byte aligned range into L2.
-  if (bytes >= 16)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)bytes)
-                 : "memory");
-}
-
-// Prefetch the 16-byte aligned interior of [p, p + bytes).
-__device__ __forceinline__ void prefetch_range(const void* p, size_t bytes) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uintptr_t lo = (a + 15) & ~uintptr_t(15);
-  const uintptr_t hi = (a + bytes) & ~uintptr_t(15);
-  size_t left = hi > lo ? hi - lo : 0;
-  uintptr_t cur = lo;
-  while (left >= 16) {
-    const size_t n = left > (size_t)(1u << 20) ? (size_t)(1u << 20) : left;
-    prefetch_l2(reinterpret_cast<const void*>(cur), n);
-    cur += n;
-    left -= n;
-  }
-}
-
 template <int UMAX>
 __global__ void __launch_bounds__(128, 3)
 ocd_projected_kernel(const DetectParams P) {
@@ -95,27 +74,8 @@ ocd_projected_kernel(const DetectParams P) {
   const long long nwarps_total = (long long)gridDim.x * (blockDim.x >> 5);
   const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
   const bool vec_h = (U % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.H) & 15u) == 0);
-  const size_t hbytes = (size_t)B * U * sizeof(float2);
-  const size_t ybytes = (size_t)T * B * sizeof(float2);
-
-  if (lane == 0) {
-    for (int a = 0; a < 2; ++a) {
-      const long long sp = gw + a * nwarps_total;
-      if (sp < P.Nsc) {
-        prefetch_range(P.H + sp * (long long)B * U, hbytes);
-        prefetch_range(P.Y + sp * (long long)T * B, ybytes);
-      }
-    }
-  }
 
   for (long long sc = gw; sc < P.Nsc; sc += nwarps_total) {
-    if (lane == 0) {
-      const long long sp = sc + 2 * nwarps_total;
-      if (sp < P.Nsc) {
-        prefetch_range(P.H + sp * (long long)B * U, hbytes);
-        prefetch_range(P.Y + sp * (long long)T * B, ybytes);
-      }
-    }
     const float2* Hs = P.H + sc * (long long)B * U;
     const float2* Ys = P.Y + sc * (long long)T * B;
 
