@@ -4,13 +4,9 @@
 
 namespace ocd {
 
-KernelFn projected_tma_kernel(int umax) {
-  return umax <= 4 ? ocd_projected_tma_kernel<4> : ocd_projected_tma_kernel<8>;
-}
+KernelFn projected_tma_kernel(int /*umax*/) { return ocd_projected_tma_kernel; }
 
-size_t projected_tma_smem_per_warp(int umax) {
-  return umax <= 4 ? TmaShape<4>::kWarpBytes : TmaShape<8>::kWarpBytes;
-}
+size_t projected_tma_smem_per_warp(int /*umax*/) { return TmaShape::kWarpBytes; }
 
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear) {
   cudaError_t e = cudaMemcpyFromSymbol(bits, g_tma_fault, sizeof(unsigned int));

@@ -11,16 +11,18 @@
 // tracked with one mbarrier per buffer; every wait has an iteration limit,
 // after which the warp records a fault in device memory and leaves.
 //
-//   GEMM (per step): lane = c + 4 g; lane (g, c) takes antennas g, g+8, ...
-//     of the block and accumulates q0 = H^H y for the pass symbols c, c+4, ...
-//     and the columns c, c+4, ... of G = H^H H (first pass only), all from
-//     shared memory.  Staged received rows are padded to a stride of 32 mod
-//     128 bytes so the four column groups hit distinct banks.
-//   Epilogue (last block of a pass): the eight antenna-group partials are
-//     summed through shared memory (reusing the drained buffer); the first
-//     pass also derives ||h_u||^2 = G_uu, d_u^-1, p_u and the soft-output
-//     constants; the K sweeps run with 32/kPass lanes per symbol; then the
-//     LLRs and xhat are written.
+//   Products (per step): q0 = H^H Y^T for the pass's 16 symbols and G = H^H H
+//     (first pass only) on the tensor cores, as real m16n8k8 TF32 MMAs over
+//     the realified K = 2B dimension with the three-term TF32 split, which
+//     keeps FP32-level accuracy.  A holds [Re H^H; Im H^H] for the 8 user
+//     slots; B is a staged received row (interleaved re/im is exactly the
+//     K layout) or, for G, the same channel entries that form A.  Staged
+//     received rows are padded to a stride of 16 mod 128 bytes so the eight
+//     rows of a fragment hit distinct banks.
+//   Epilogue (last block of a pass): the accumulator fragments go to shared
+//     memory; the first pass also derives ||h_u||^2 = G_uu, d_u^-1, p_u and
+//     the soft-output constants; the K sweeps run with two lanes per symbol;
+//     then the LLRs and xhat are written.
 #pragma once
 
 #include "ocd_common.cuh"
@@ -29,28 +31,22 @@ namespace ocd {
 
 constexpr int kTmaWaitLimit = 1 << 22;  // try_wait polls before a wait is declared failed
 
-template <int UMAX>
+// Per-warp geometry of the bulk-copy kernel (users padded to 8: the MMA tile
+// has 16 rows = real and imaginary parts of 8 users).
 struct TmaShape {
-  static constexpr int kAG = 8;                            // antenna groups
-  static constexpr int kCG = 4;                            // column groups
-  static constexpr int kTS = 32 / UMAX;                    // pass symbols per lane
-  static constexpr int kPass = kCG * kTS;                  // symbols per pass
-  static constexpr int kGC = UMAX / kCG;                   // G columns per lane
-  static constexpr int kVals = 2 * (kTS * UMAX + UMAX * kGC);  // partial floats per lane
-  static constexpr int kRedStride = kVals | 1;             // odd: conflict-free stores
-  static constexpr int kBB = UMAX == 8 ? 64 : 32;          // antennas per block
-  static constexpr int kYRow = kBB * 8 + 32;               // staged Y row stride (bytes)
-  static constexpr int kHBytes = kBB * UMAX * 8;           // staged H block (bytes)
+  static constexpr int kUsers = 8;                          // user slots
+  static constexpr int kPass = 16;                          // symbols per pass (2 MMA n-tiles)
+  static constexpr int kBB = 64;                            // antennas per staged block
+  static constexpr int kYRow = kBB * 8 + 16;                // staged Y row stride (16 mod 128)
+  static constexpr int kHBytes = kBB * kUsers * 8;          // staged H block (bytes)
   static constexpr int kBufBytes = kHBytes + kPass * kYRow;
-  static constexpr int kRedBytes = 32 * kRedStride * 4;
-  static_assert(kRedBytes <= kBufBytes, "reduction area must fit a drained buffer");
-  static constexpr int kHalves = 32 / kPass;               // sweep lanes per symbol
-  static constexpr int kUP = UMAX / kHalves;               // users per sweep lane
+  static constexpr int kHalves = 2;                         // sweep lanes per symbol
+  static constexpr int kUP = kUsers / kHalves;              // users per sweep lane
   // per-warp byte offsets
-  static constexpr int kOffQ = 2 * kBufBytes;              // q0, later z [pass symbol][u]
-  static constexpr int kOffG = kOffQ + 8 * kPass * UMAX;   // full G [i][j]
-  static constexpr int kOffPre = kOffG + 8 * UMAX * UMAX;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
-  static constexpr int kOffBar = kOffPre + 16 * UMAX;      // two mbarriers
+  static constexpr int kOffQ = 2 * kBufBytes;               // q0, later z [pass symbol][u]
+  static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;  // full G [i][j]
+  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
+  static constexpr int kOffBar = kOffPre + 16 * kUsers;     // two mbarriers
   static constexpr int kWarpBytes = kOffBar + 16;
 };
 
@@ -100,14 +96,42 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // this header; the host reads it through projected_tma_fault().
 __device__ unsigned int g_tma_fault = 0;
 
-template <int UMAX>
+// TF32 tensor-core helpers.  A product is carried as three TF32 products
+// (hi*hi + hi*lo + lo*hi, the split of Ootomo and Yokota), which keeps the
+// result at FP32-level accuracy: hi = round-to-nearest TF32 of x, lo = x - hi
+// (exact in FP32; the tensor core reads its leading 19 bits).
+__device__ __forceinline__ uint32_t tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_hi(x);
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+// D += A B for one m16n8k8 TF32 tile (A row-major 16x8, B column-major 8x8).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma3_tf32(float (&d)[4], const uint32_t (&ah)[4],
+                                          const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
+                                          uint32_t bl0, uint32_t bl1) {
+  mma_tf32(d, al, bh0, bh1);
+  mma_tf32(d, ah, bl0, bl1);
+  mma_tf32(d, ah, bh0, bh1);
+}
+
 __global__ void __launch_bounds__(128, 2)
 ocd_projected_tma_kernel(const DetectParams P) {
-  using S = TmaShape<UMAX>;
-  constexpr int TS = S::kTS;
-  constexpr int GC = S::kGC;
+  using S = TmaShape;
   constexpr int BB = S::kBB;
   constexpr int UP = S::kUP;
+  constexpr int NU = S::kUsers;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -120,8 +144,9 @@ ocd_projected_tma_kernel(const DetectParams P) {
   const int U = P.U;
   const int B = P.B;
   const int T = P.T;
-  const int c = lane & 3;
-  const int g = lane >> 2;
+  // MMA fragment coordinates: row group gq (user / symbol within a tile), thread t
+  const int gq = lane >> 2;
+  const int t = lane & 3;
   const long long nW = (long long)gridDim.x * (blockDim.x >> 5);
   const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
   const int nblk = (B + BB - 1) / BB;
@@ -164,8 +189,9 @@ ocd_projected_tma_kernel(const DetectParams P) {
     }
   };
 
-  float qa[TS][UMAX][2];
-  float ga[UMAX][GC][2];
+  // Accumulator tiles: [0], [1] = q0 for pass symbols 0-7, 8-15; [2] = G.
+  // Rows 0-7 hold real parts and rows 8-15 imaginary parts of user gq.
+  float acc[3][4];
   uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
 
   issue(0, 0);
@@ -192,123 +218,91 @@ ocd_projected_tma_kernel(const DetectParams P) {
     const bool first = pass == 0;
     const unsigned char* bp = ws + buf * S::kBufBytes;
     const float2* sH = reinterpret_cast<const float2*>(bp);
+    const float* sY = reinterpret_cast<const float*>(bp + S::kHBytes);
 
     if (blk == 0) {
 #pragma unroll
-      for (int i = 0; i < TS; ++i)
+      for (int n = 0; n < 3; ++n)
 #pragma unroll
-        for (int u = 0; u < UMAX; ++u) { qa[i][u][0] = 0.0f; qa[i][u][1] = 0.0f; }
-#pragma unroll
-      for (int i = 0; i < UMAX; ++i)
-#pragma unroll
-        for (int m = 0; m < GC; ++m) { ga[i][m][0] = 0.0f; ga[i][m][1] = 0.0f; }
+        for (int e = 0; e < 4; ++e) acc[n][e] = 0.0f;
     }
 
-    // ---------------- GEMM over this block's antennas ----------------------
-#pragma unroll 2
-    for (int b = g; b < bb; b += S::kAG) {
-      float2 h[UMAX];
-      const float2* row = sH + b * U;
-      if ((U & 1) == 0) {
-#pragma unroll
-        for (int u = 0; u < UMAX; u += 2) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (u < U) v = *reinterpret_cast<const float4*>(row + u);
-          h[u] = make_float2(v.x, v.y);
-          h[u + 1] = make_float2(v.z, v.w);
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < UMAX; ++u) h[u] = u < U ? row[u] : make_float2(0.f, 0.f);
+    // ---------------- products on the tensor cores ------------------------
+    // Realified K index k = 2b + (0: real, 1: imaginary) over this block's
+    // antennas b; one k-step covers 4 antennas.  A = [Re H^H; Im H^H] rows:
+    //   A[u][2b] = Re h_bu, A[u][2b+1] = Im h_bu,
+    //   A[8+u][2b] = -Im h_bu, A[8+u][2b+1] = Re h_bu,
+    // so A x (x = interleaved complex column) gives Re and Im of h_u^H x.
+    const bool user_ok = gq < U;
+    const bool sym0 = gq < np;       // symbol gq of tile 0
+    const bool sym1 = gq + 8 < np;   // symbol gq + 8 of tile 1
+    const float* y0 = sY + gq * (S::kYRow / 4);
+    const float* y1 = sY + (gq + 8) * (S::kYRow / 4);
+    for (int kb = 0; kb < bb; kb += 4) {
+      // A fragment: antennas kb + t/2 and kb + 2 + t/2 of user gq
+      const int ba = kb + (t >> 1);
+      const int bc = ba + 2;
+      float2 ha = make_float2(0.f, 0.f), hc = make_float2(0.f, 0.f);
+      if (user_ok) {
+        if (ba < bb) ha = sH[ba * U + gq];
+        if (bc < bb) hc = sH[bc * U + gq];
       }
-      float2 y[TS];
-#pragma unroll
-      for (int i = 0; i < TS; ++i) {
-        const int ts = c + S::kCG * i;
-        y[i] = ts < np ? *reinterpret_cast<const float2*>(bp + S::kHBytes + ts * S::kYRow + b * 8)
-                       : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int i = 0; i < TS; ++i)
-#pragma unroll
-        for (int u = 0; u < UMAX; ++u) {
-          // q0[t][u] += conj(h[b][u]) y[t][b]
-          float re = qa[i][u][0], im = qa[i][u][1];
-          re = fmaf(h[u].x, y[i].x, re);
-          re = fmaf(h[u].y, y[i].y, re);
-          im = fmaf(h[u].x, y[i].y, im);
-          im = fmaf(-h[u].y, y[i].x, im);
-          qa[i][u][0] = re;
-          qa[i][u][1] = im;
-        }
-      if (first) {
-#pragma unroll
-        for (int m = 0; m < GC; ++m) {
-          const int j = c + S::kCG * m;
-          const float2 hj = j < U ? row[j] : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int i = 0; i < UMAX; ++i) {
-            // G[i][j] += conj(h[b][i]) h[b][j]
-            float re = ga[i][m][0], im = ga[i][m][1];
-            re = fmaf(h[i].x, hj.x, re);
-            re = fmaf(h[i].y, hj.y, re);
-            im = fmaf(h[i].x, hj.y, im);
-            im = fmaf(-h[i].y, hj.x, im);
-            ga[i][m][0] = re;
-            ga[i][m][1] = im;
-          }
-        }
-      }
+      const bool re = (t & 1) == 0;
+      const float a0 = re ? ha.x : ha.y;
+      const float a1 = re ? -ha.y : ha.x;
+      const float a2 = re ? hc.x : hc.y;
+      const float a3 = re ? -hc.y : hc.x;
+      uint32_t ah[4], al[4];
+      split_tf32(a0, ah[0], al[0]);
+      split_tf32(a1, ah[1], al[1]);
+      split_tf32(a2, ah[2], al[2]);
+      split_tf32(a3, ah[3], al[3]);
+      // B fragments of the received rows: x[k][n] = Y[n] float 2*b0 + k
+      const int kf = 2 * kb + t;  // float offset of k = t within this block row
+      const bool k0ok = kf < 2 * bb;
+      const bool k1ok = kf + 4 < 2 * bb;
+      const float y00 = (sym0 && k0ok) ? y0[kf] : 0.0f;
+      const float y01 = (sym0 && k1ok) ? y0[kf + 4] : 0.0f;
+      const float y10 = (sym1 && k0ok) ? y1[kf] : 0.0f;
+      const float y11 = (sym1 && k1ok) ? y1[kf + 4] : 0.0f;
+      uint32_t bh00, bl00, bh01, bl01, bh10, bl10, bh11, bl11;
+      split_tf32(y00, bh00, bl00);
+      split_tf32(y01, bh01, bl01);
+      split_tf32(y10, bh10, bl10);
+      split_tf32(y11, bh11, bl11);
+      mma3_tf32(acc[0], ah, al, bh00, bh01, bl00, bl01);
+      mma3_tf32(acc[1], ah, al, bh10, bh11, bl10, bl11);
+      // G: the B column j = gq is h_j, whose (k, j) entries are exactly this
+      // lane's A entries of rows 0-7: b0 = a0, b1 = a2.
+      if (first) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
     }
     __syncwarp();
     if (blk != nblk - 1) continue;
 
     // ---------------- epilogue of a pass ----------------------------------
-    // (1) partial sums -> drained buffer; sum the eight antenna groups
-    float* red = reinterpret_cast<float*>(ws + buf * S::kBufBytes);
-    {
-      float* mine = red + lane * S::kRedStride;
+    // (1) fragments -> shared memory.  Lane (gq, t) holds rows gq (real) and
+    // gq + 8 (imaginary) of columns 2t, 2t + 1 of each tile.
 #pragma unroll
-      for (int i = 0; i < TS; ++i)
+    for (int n = 0; n < 2; ++n)
 #pragma unroll
-        for (int u = 0; u < UMAX; ++u) {
-          mine[2 * (i * UMAX + u)] = qa[i][u][0];
-          mine[2 * (i * UMAX + u) + 1] = qa[i][u][1];
-        }
-      if (first) {
-#pragma unroll
-        for (int i = 0; i < UMAX; ++i)
-#pragma unroll
-          for (int m = 0; m < GC; ++m) {
-            mine[2 * (TS * UMAX + i * GC + m)] = ga[i][m][0];
-            mine[2 * (TS * UMAX + i * GC + m) + 1] = ga[i][m][1];
-          }
+      for (int e = 0; e < 2; ++e) {
+        const int ts = 8 * n + 2 * t + e;
+        sq[2 * (ts * NU + gq)] = acc[n][e];
+        sq[2 * (ts * NU + gq) + 1] = acc[n][2 + e];
       }
-    }
-    __syncwarp();
-    const int nv = first ? S::kVals : 2 * TS * UMAX;
-    for (int f = lane; f < S::kCG * nv; f += 32) {
-      const int cc = f / nv;
-      const int v = f - cc * nv;
-      float acc = 0.0f;
+    if (first) {
 #pragma unroll
-      for (int gg = 0; gg < S::kAG; ++gg) acc += red[(cc + S::kCG * gg) * S::kRedStride + v];
-      if (v < 2 * TS * UMAX) {
-        const int i = (v >> 1) / UMAX;
-        const int u = (v >> 1) - i * UMAX;
-        sq[2 * ((cc + S::kCG * i) * UMAX + u) + (v & 1)] = acc;
-      } else {
-        const int e = (v >> 1) - TS * UMAX;
-        const int i = e / GC;
-        const int j = cc + S::kCG * (e - i * GC);
-        sg[2 * (i * UMAX + j) + (v & 1)] = acc;
+      for (int e = 0; e < 2; ++e) {
+        const int j = 2 * t + e;
+        sg[2 * (gq * NU + j)] = acc[2][e];
+        sg[2 * (gq * NU + j) + 1] = acc[2][2 + e];
       }
     }
     __syncwarp();
     // (2) preprocessing (Algorithm 1) and soft-output constants
     if (first) {
-      if (lane < UMAX) {
-        const float nrm = sg[2 * (lane * UMAX + lane)];
+      if (lane < NU) {
+        const float nrm = sg[2 * (lane * NU + lane)];
         const float den = nrm + P.alpha;
         const float dinv = (lane < U && den > 0.0f) ? 1.0f / den : 0.0f;
         const float p = dinv * nrm;
@@ -316,30 +310,30 @@ ocd_projected_tma_kernel(const DetectParams P) {
         spre[4 * lane + 1] = p;
         spre[4 * lane + 2] = nrm;
         spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
-        sg[2 * (lane * UMAX + lane) + 1] = 0.0f;  // G_uu is real
+        sg[2 * (lane * NU + lane) + 1] = 0.0f;  // G_uu is real
       }
       __syncwarp();
     }
-    // (3) K sweeps on q: lane = kHalves * ts + hf holds users [hf*UP, hf*UP+UP)
+    // (3) K sweeps on q: lane = 2 ts + hf holds users [hf*UP, hf*UP + UP)
     {
-      const int ts = lane / S::kHalves;
-      const int hf = lane - ts * S::kHalves;
+      const int ts = lane >> 1;
+      const int hf = lane & 1;
       const bool act = ts < np;
       float qr[UP], qi[UP], zr[UP], zi[UP];
 #pragma unroll
       for (int l = 0; l < UP; ++l) {
         const int j = hf * UP + l;
-        qr[l] = act ? sq[2 * (ts * UMAX + j)] : 0.0f;
-        qi[l] = act ? sq[2 * (ts * UMAX + j) + 1] : 0.0f;
+        qr[l] = act ? sq[2 * (ts * NU + j)] : 0.0f;
+        qi[l] = act ? sq[2 * (ts * NU + j) + 1] : 0.0f;
         zr[l] = 0.0f;
         zi[l] = 0.0f;
       }
       for (int k = 0; k < P.K; ++k) {
 #pragma unroll
-        for (int u = 0; u < UMAX; ++u) {
+        for (int u = 0; u < NU; ++u) {
           if (u < U) {
-            const int lu = u % UP;         // compile-time slot of user u
-            const int oh = u / UP;         // half that owns user u
+            const int lu = u % UP;  // compile-time slot of user u
+            const int oh = u / UP;  // half that owns user u
             const float dinv = spre[4 * u];
             const float pu = spre[4 * u + 1];
             // z_u <- proj(d_u^-1 q_u + p_u z_u) on the owning lane
@@ -350,16 +344,14 @@ ocd_projected_tma_kernel(const DetectParams P) {
             float di = wi - zi[lu];
             const bool own = hf == oh;
             if (own) { zr[lu] = wr; zi[lu] = wi; }
-            if (S::kHalves == 2) {
-              const float pr = __shfl_xor_sync(kFullMask, dr, 1);
-              const float pi = __shfl_xor_sync(kFullMask, di, 1);
-              if (!own) { dr = pr; di = pi; }
-            }
+            const float pr = __shfl_xor_sync(kFullMask, dr, 1);
+            const float pi = __shfl_xor_sync(kFullMask, di, 1);
+            if (!own) { dr = pr; di = pi; }
             // q <- q - G[:, u] dz for my users
 #pragma unroll
             for (int l = 0; l < UP; ++l) {
               const int j = hf * UP + l;
-              const float2 gju = *reinterpret_cast<const float2*>(sg + 2 * (j * UMAX + u));
+              const float2 gju = *reinterpret_cast<const float2*>(sg + 2 * (j * NU + u));
               qr[l] = fmaf(-gju.x, dr, fmaf(gju.y, di, qr[l]));
               qi[l] = fmaf(-gju.x, di, fmaf(-gju.y, dr, qi[l]));
             }
@@ -371,8 +363,8 @@ ocd_projected_tma_kernel(const DetectParams P) {
 #pragma unroll
         for (int l = 0; l < UP; ++l) {
           const int j = hf * UP + l;
-          sq[2 * (ts * UMAX + j)] = zr[l];  // z overwrites q0
-          sq[2 * (ts * UMAX + j) + 1] = zi[l];
+          sq[2 * (ts * NU + j)] = zr[l];  // z overwrites q0
+          sq[2 * (ts * NU + j) + 1] = zi[l];
         }
       }
       __syncwarp();
@@ -381,7 +373,7 @@ ocd_projected_tma_kernel(const DetectParams P) {
     for (int f = lane; f < np * U; f += 32) {
       const int ts = f / U;
       const int u = f - ts * U;
-      const float2 z = make_float2(sq[2 * (ts * UMAX + u)], sq[2 * (ts * UMAX + u) + 1]);
+      const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
       const long long o = (sc * T + tb + ts) * U + u;
       if (P.xhat) P.xhat[o] = z;
       if (P.llr) {
