@@ -97,10 +97,10 @@ int device_info(int dev, DeviceInfo& out) {
       e = cudaFuncSetAttribute(ocd::projected_kernel(umax),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      e = cudaFuncSetAttribute(ocd::projected_tma_kernel(umax),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
+    e = cudaFuncSetAttribute(ocd::projected_tma_kernel_ptr(),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -188,19 +188,32 @@ bool tma_eligible(const ocd::DetectParams& P) {
 }
 
 int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
-  const int umax = U <= 4 ? 4 : 8;
-  const bool tma = tma_eligible(P);
-  KernelFn fn = tma ? ocd::projected_tma_kernel(umax) : ocd::projected_kernel(umax);
   const int nt = 128;
-  const size_t smem = (nt / 32) * (tma ? ocd::projected_tma_smem_per_warp(umax)
-                                       : ocd::projected_smem_per_warp(umax));
+  const long long need = (P.Nsc + nt / 32 - 1) / (nt / 32);  // one warp per subcarrier
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
+  cudaError_t e;
+  if (tma_eligible(P)) {
+    const size_t smem = ocd::projected_tma_smem_per_cta();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ocd::projected_tma_kernel_ptr(), nt,
+                                                      smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm >= 1) {
+      long long grid = (long long)di.sms * per_sm;
+      if (grid > need) grid = need;
+      e = ocd::launch_projected_tma(P, (unsigned)grid, stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) return OCD_OK;
+      // no tensor-map encoder in this driver: the load-based variant follows
+      if (e != cudaErrorNotSupported) return cuda_fail(e, "projected kernel launch");
+    }
+  }
+  const int umax = U <= 4 ? 4 : 8;
+  KernelFn fn = ocd::projected_kernel(umax);
+  const size_t smem = (nt / 32) * ocd::projected_smem_per_warp(umax);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (per_sm < 1) return fail(OCD_ERR_UNSUPPORTED, "projected kernel cannot be resident");
-  const long long warps_needed = P.Nsc;
   long long grid = (long long)di.sms * per_sm;
-  const long long need = (warps_needed + nt / 32 - 1) / (nt / 32);
   if (grid > need) grid = need;
   void* args[] = {&P};
   e = cudaLaunchKernel((const void*)fn, dim3((unsigned)grid), dim3(nt), args, smem, stream);

@@ -45,9 +45,13 @@ KernelFn residual_kernel(int npp, int s);
 KernelFn projected_kernel(int umax);
 size_t projected_smem_per_warp(int umax);
 constexpr int kProjectedMaxUsers = 8;
-// Bulk-copy (TMA) projected kernels: needs even B and 16-byte aligned H, Y.
-KernelFn projected_tma_kernel(int umax);
-size_t projected_tma_smem_per_warp(int umax);
+// Bulk-copy (TMA) projected kernel: needs even B and 16-byte aligned H, Y
+// (128 threads per CTA).  launch_projected_tma encodes the tensor map of Y
+// and launches; cudaErrorNotSupported means the driver offers no tensor-map
+// encoder.
+const void* projected_tma_kernel_ptr();
+size_t projected_tma_smem_per_cta();
+cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream);
 // Reads (and optionally clears) the fault word of the bulk-copy kernels;
 // synchronous with respect to the device.
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear);

@@ -1,12 +1,56 @@
-// Instances of the bulk-copy (TMA) projected-residual OCD kernel and its
-// fault word.
+// Bulk-copy (TMA) projected-residual OCD kernel: tensor-map encoding,
+// launch, and the fault word.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "ocd_projected_tma.cuh"
 
 namespace ocd {
 
-KernelFn projected_tma_kernel(int /*umax*/) { return ocd_projected_tma_kernel; }
+namespace {
 
-size_t projected_tma_smem_per_warp(int /*umax*/) { return TmaShape::kWarpBytes; }
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+const void* projected_tma_kernel_ptr() {
+  return reinterpret_cast<const void*>(ocd_projected_tma_kernel);
+}
+
+size_t projected_tma_smem_per_cta() { return 4 * TmaShape::kWarpBytes + 1024; }
+
+cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // Y as a 2-D float tensor: rows = (subcarrier, symbol), 2B floats per row.
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {2ull * (cuuint64_t)P.B, (cuuint64_t)P.Nsc * (cuuint64_t)P.T};
+  const cuuint64_t strides[1] = {2ull * (cuuint64_t)P.B * sizeof(float)};
+  const cuuint32_t box[2] = {2 * TmaShape::kBoxAnt, TmaShape::kPass};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(P.Y), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  DetectParams p = P;
+  void* args[] = {&p, &map};
+  return cudaLaunchKernel(projected_tma_kernel_ptr(), dim3(grid), dim3(128), args,
+                          projected_tma_smem_per_cta(), stream);
+}
 
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear) {
   cudaError_t e = cudaMemcpyFromSymbol(bits, g_tma_fault, sizeof(unsigned int));

@@ -5,9 +5,10 @@
 // One warp owns one subcarrier at a time and walks a sequence of steps:
 // for each subcarrier, for each pass of kPass symbols, for each block of BB
 // antennas.  Each step's operands -- the BB channel rows H[b0 .. b0+BB)[:]
-// (one contiguous copy) and the BB-antenna slices of the pass's received
-// rows (one copy per symbol) -- land in one of two per-warp buffers; the
-// copy of step s+1 is in flight while step s is computed.  Completion is
+// (one contiguous bulk copy) and the pass's received rows restricted to the
+// block (one 2-D tensor copy per 16 antennas x 16 symbols, 128-byte
+// swizzled) -- land in one of kStages per-warp buffers; the copies of the
+// next kStages - 1 steps are in flight while a step is computed.  Completion is
 // tracked with one mbarrier per buffer; every wait has an iteration limit,
 // after which the warp records a fault in device memory and leaves.
 //
@@ -16,14 +17,14 @@
 //     the realified K = 2B dimension with the three-term TF32 split, which
 //     keeps FP32-level accuracy.  A holds [Re H^H; Im H^H] for the 8 user
 //     slots; B is a staged received row (interleaved re/im is exactly the
-//     K layout) or, for G, the same channel entries that form A.  Staged
-//     received rows are padded to a stride of 16 mod 128 bytes so the eight
-//     rows of a fragment hit distinct banks.
+//     K layout) or, for G, the same channel entries that form A.
 //   Epilogue (last block of a pass): the accumulator fragments go to shared
 //     memory; the first pass also derives ||h_u||^2 = G_uu, d_u^-1, p_u and
 //     the soft-output constants; the K sweeps run with two lanes per symbol;
 //     then the LLRs and xhat are written.
 #pragma once
+
+#include <cuda.h>  // CUtensorMap (type only; no driver library is linked)
 
 #include "ocd_common.cuh"
 
@@ -33,21 +34,37 @@ constexpr int kTmaWaitLimit = 1 << 22;  // try_wait polls before a wait is decla
 
 // Per-warp geometry of the bulk-copy kernel (users padded to 8: the MMA tile
 // has 16 rows = real and imaginary parts of 8 users).
+#ifndef OCD_TMA_BLOCK
+#define OCD_TMA_BLOCK 64      // antennas per staged block
+#endif
+#ifndef OCD_TMA_MIN_CTAS
+#define OCD_TMA_MIN_CTAS 2    // resident CTAs per SM the register budget targets
+#endif
+#ifndef OCD_TMA_STAGES
+#define OCD_TMA_STAGES 2      // staging buffers per warp (steps in flight + 1)
+#endif
+
 struct TmaShape {
   static constexpr int kUsers = 8;                          // user slots
   static constexpr int kPass = 16;                          // symbols per pass (2 MMA n-tiles)
-  static constexpr int kBB = 64;                            // antennas per staged block
-  static constexpr int kYRow = kBB * 8 + 16;                // staged Y row stride (16 mod 128)
+  static constexpr int kBB = OCD_TMA_BLOCK;                 // antennas per staged block
+  static constexpr int kBoxAnt = 16;                        // antennas per Y box (128 B rows)
+  static constexpr int kBoxBytes = kPass * 128;             // one swizzled Y box
+  static constexpr int kBoxes = kBB / kBoxAnt;              // Y boxes per block
+  static constexpr int kYBytes = kBoxes * kBoxBytes;
   static constexpr int kHBytes = kBB * kUsers * 8;          // staged H block (bytes)
-  static constexpr int kBufBytes = kHBytes + kPass * kYRow;
+  static constexpr int kBufBytes = kYBytes + kHBytes;       // multiple of 1024
+  static constexpr int kStages = OCD_TMA_STAGES;
   static constexpr int kHalves = 2;                         // sweep lanes per symbol
   static constexpr int kUP = kUsers / kHalves;              // users per sweep lane
-  // per-warp byte offsets
-  static constexpr int kOffQ = 2 * kBufBytes;               // q0, later z [pass symbol][u]
+  // per-warp byte offsets (the warp area is 1024-byte aligned for the swizzle)
+  static constexpr int kOffQ = kStages * kBufBytes;         // q0, later z [pass symbol][u]
   static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;  // full G [i][j]
   static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
-  static constexpr int kOffBar = kOffPre + 16 * kUsers;     // two mbarriers
-  static constexpr int kWarpBytes = kOffBar + 16;
+  static constexpr int kOffBar = kOffPre + 16 * kUsers;     // one mbarrier per buffer
+  static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
+  static_assert(kBB % kBoxAnt == 0, "blocks are whole Y boxes");
+  static_assert(kBufBytes % 1024 == 0, "swizzled boxes need 1024-byte alignment");
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -71,6 +88,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// 2-D tiled tensor copy (TMA) of one box at coordinates (x, y) into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -98,15 +124,11 @@ __device__ unsigned int g_tma_fault = 0;
 
 // TF32 tensor-core helpers.  A product is carried as three TF32 products
 // (hi*hi + hi*lo + lo*hi, the split of Ootomo and Yokota), which keeps the
-// result at FP32-level accuracy: hi = round-to-nearest TF32 of x, lo = x - hi
-// (exact in FP32; the tensor core reads its leading 19 bits).
-__device__ __forceinline__ uint32_t tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// result at FP32-level accuracy: hi = x with the 13 low mantissa bits
+// cleared (a TF32 value), lo = x - hi (exact in FP32; the tensor core reads
+// its leading 19 bits).  Relative error of a split product: about 2^-20.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_hi(x);
+  hi = __float_as_uint(x) & 0xffffe000u;
   lo = __float_as_uint(x - __uint_as_float(hi));
 }
 // D += A B for one m16n8k8 TF32 tile (A row-major 16x8, B column-major 8x8).
@@ -126,16 +148,20 @@ __device__ __forceinline__ void mma3_tf32(float (&d)[4], const uint32_t (&ah)[4]
   mma_tf32(d, ah, bh0, bh1);
 }
 
-__global__ void __launch_bounds__(128, 2)
-ocd_projected_tma_kernel(const DetectParams P) {
+// ymap: Y viewed as a 2-D float tensor [Nsc*T rows][2B floats], box 32 x 16
+// (16 antennas x 16 symbols), 128-byte swizzle, out-of-range elements zero.
+__global__ void __launch_bounds__(128, OCD_TMA_MIN_CTAS)
+ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorMap ymap) {
   using S = TmaShape;
   constexpr int BB = S::kBB;
   constexpr int UP = S::kUP;
   constexpr int NU = S::kUsers;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  unsigned char* ws = smem_raw + warp * S::kWarpBytes;
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* ws = base + warp * S::kWarpBytes;
   float* sq = reinterpret_cast<float*>(ws + S::kOffQ);
   float* sg = reinterpret_cast<float*>(ws + S::kOffG);
   float* spre = reinterpret_cast<float*>(ws + S::kOffPre);
@@ -157,8 +183,7 @@ ocd_projected_tma_kernel(const DetectParams P) {
   if (nsteps == 0) return;
 
   if (lane == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
+    for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -176,16 +201,17 @@ ocd_projected_tma_kernel(const DetectParams P) {
     const int np = min(S::kPass, T - tb);
     const uint32_t bar = bar0 + 8 * buf;
     unsigned char* bp = ws + buf * S::kBufBytes;
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(bb * U * 8 + np * bb * 8));
+    const int nbox = (bb + S::kBoxAnt - 1) / S::kBoxAnt;
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nbox * S::kBoxBytes + bb * U * 8));
     __syncwarp();
     fence_proxy_async();
-    if (lane < np) {
-      const float2* src = P.Y + ((sc * T + tb + lane) * (long long)B + b0);
-      bulk_g2s(smem_addr(bp + S::kHBytes + lane * S::kYRow), src, (uint32_t)(bb * 8), bar);
-    }
+    (void)np;
+    if (lane < nbox)
+      tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), &ymap, 2 * (b0 + S::kBoxAnt * lane),
+                  (int)(sc * T + tb), bar);
     if (lane == 31) {
       const float2* src = P.H + (sc * (long long)B + b0) * U;
-      bulk_g2s(smem_addr(bp), src, (uint32_t)(bb * U * 8), bar);
+      bulk_g2s(smem_addr(bp + S::kYBytes), src, (uint32_t)(bb * U * 8), bar);
     }
   };
 
@@ -194,14 +220,24 @@ ocd_projected_tma_kernel(const DetectParams P) {
   float acc[3][4];
   uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
 
-  issue(0, 0);
+  // prologue: the first kStages - 1 steps in flight
+  for (int i = 0; i < S::kStages - 1 && i < nsteps; ++i) issue(i, i);
   for (long long s = 0; s < nsteps; ++s) {
-    const int buf = (int)(s & 1);
-    if (s + 1 < nsteps) issue(s + 1, buf ^ 1);
+    const int buf = (int)(s % S::kStages);
+    {
+      const long long ahead = s + S::kStages - 1;
+      if (ahead < nsteps) issue(ahead, (int)(ahead % S::kStages));
+    }
     if (!mbar_wait(bar0 + 8 * buf, (parity >> buf) & 1)) {
       if (lane == 0) atomicOr(&g_tma_fault, 1u);
       // let the copies already in flight finish (bounded) before leaving
-      if (s + 1 < nsteps) mbar_wait(bar0 + 8 * (buf ^ 1), (parity >> (buf ^ 1)) & 1);
+      for (int i = 1; i < S::kStages; ++i) {
+        const long long sp = s + i;
+        if (sp < nsteps) {
+          const int bi = (int)(sp % S::kStages);
+          mbar_wait(bar0 + 8 * bi, (parity >> bi) & 1);
+        }
+      }
       return;
     }
     parity ^= 1u << buf;
@@ -217,8 +253,7 @@ ocd_projected_tma_kernel(const DetectParams P) {
     const int np = min(S::kPass, T - tb);
     const bool first = pass == 0;
     const unsigned char* bp = ws + buf * S::kBufBytes;
-    const float2* sH = reinterpret_cast<const float2*>(bp);
-    const float* sY = reinterpret_cast<const float*>(bp + S::kHBytes);
+    const float2* sH = reinterpret_cast<const float2*>(bp + S::kYBytes);
 
     if (blk == 0) {
 #pragma unroll
@@ -228,53 +263,53 @@ ocd_projected_tma_kernel(const DetectParams P) {
     }
 
     // ---------------- products on the tensor cores ------------------------
-    // Realified K index k = 2b + (0: real, 1: imaginary) over this block's
-    // antennas b; one k-step covers 4 antennas.  A = [Re H^H; Im H^H] rows:
-    //   A[u][2b] = Re h_bu, A[u][2b+1] = Im h_bu,
-    //   A[8+u][2b] = -Im h_bu, A[8+u][2b+1] = Re h_bu,
-    // so A x (x = interleaved complex column) gives Re and Im of h_u^H x.
-    const bool user_ok = gq < U;
-    const bool sym0 = gq < np;       // symbol gq of tile 0
-    const bool sym1 = gq + 8 < np;   // symbol gq + 8 of tile 1
-    const float* y0 = sY + gq * (S::kYRow / 4);
-    const float* y1 = sY + (gq + 8) * (S::kYRow / 4);
-    for (int kb = 0; kb < bb; kb += 4) {
-      // A fragment: antennas kb + t/2 and kb + 2 + t/2 of user gq
-      const int ba = kb + (t >> 1);
-      const int bc = ba + 2;
-      float2 ha = make_float2(0.f, 0.f), hc = make_float2(0.f, 0.f);
-      if (user_ok) {
-        if (ba < bb) ha = sH[ba * U + gq];
-        if (bc < bb) hc = sH[bc * U + gq];
+    // A k-step covers 4 antennas a_j = base + kb + {0, 1, 8, 9}[j] of a
+    // 16-antenna box (kb = 0, 2, 4, 6); realified K index j (0..3) is the
+    // real part of antenna a_j and 4 + j its imaginary part.
+    // A = [Re H^H; Im H^H] over the 8 user slots:
+    //   A[u][j] = Re h_{a_j,u}    A[u][4+j] = Im h_{a_j,u}
+    //   A[8+u][j] = -Im h_{a_j,u}   A[8+u][4+j] = Re h_{a_j,u}
+    // so A x (x = [Re x_a, Im x_a]) gives Re and Im of h_u^H x.  Lane (gq, t)
+    // loads h_{a_t,gq} once: a0 = Re, a2 = Im, a3 = Re, a1 = -Im; its B
+    // entries of received row n are Re and Im of y_{n,a_t}, read from the
+    // swizzled box (16-byte chunk c of row r sits at chunk c ^ (r & 7)); the
+    // antenna order {0, 1, 8, 9} puts the 16 lanes of a half-warp on 16
+    // distinct bank slots.  Rows of A beyond U and columns beyond the pass's
+    // symbols only reach discarded outputs; antennas beyond B arrive as zeros
+    // from the tensor copy, and staged channel rows beyond the block are
+    // masked.
+    const bool tail = bb < BB;
+    const int ta = ((t >> 1) << 3) | (t & 1);   // {0, 1, 8, 9}[t]
+    const int r0 = gq, r1 = gq + 8;
+    for (int box = 0; box * S::kBoxAnt < bb; ++box) {
+      const unsigned char* yb = bp + box * S::kBoxBytes;
+#pragma unroll
+      for (int kb = 0; kb < 8; kb += 2) {
+        const int a = box * S::kBoxAnt + kb + ta;
+        const float2 h = (!tail || a < bb) ? sH[a * U + gq] : make_float2(0.f, 0.f);
+        const int chunk = (kb >> 1) + ((t >> 1) << 2);
+        const float2 ya = *reinterpret_cast<const float2*>(
+            yb + r0 * 128 + ((chunk ^ (r0 & 7)) << 4) + ((t & 1) << 3));
+        const float2 yc = *reinterpret_cast<const float2*>(
+            yb + r1 * 128 + ((chunk ^ (r1 & 7)) << 4) + ((t & 1) << 3));
+        uint32_t ah[4], al[4];
+        split_tf32(h.x, ah[0], al[0]);
+        split_tf32(h.y, ah[2], al[2]);
+        ah[3] = ah[0];
+        al[3] = al[0];
+        ah[1] = ah[2] ^ 0x80000000u;  // -Im h
+        al[1] = al[2] ^ 0x80000000u;
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(ya.x, bh0, bl0);
+        split_tf32(ya.y, bh1, bl1);
+        mma3_tf32(acc[0], ah, al, bh0, bh1, bl0, bl1);
+        split_tf32(yc.x, bh0, bl0);
+        split_tf32(yc.y, bh1, bl1);
+        mma3_tf32(acc[1], ah, al, bh0, bh1, bl0, bl1);
+        // G: the B column j = gq is h_j, whose (k, j) entries are this lane's
+        // A entries of rows 0-7: b0 = a0 = Re, b1 = a2 = Im.
+        if (first) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
       }
-      const bool re = (t & 1) == 0;
-      const float a0 = re ? ha.x : ha.y;
-      const float a1 = re ? -ha.y : ha.x;
-      const float a2 = re ? hc.x : hc.y;
-      const float a3 = re ? -hc.y : hc.x;
-      uint32_t ah[4], al[4];
-      split_tf32(a0, ah[0], al[0]);
-      split_tf32(a1, ah[1], al[1]);
-      split_tf32(a2, ah[2], al[2]);
-      split_tf32(a3, ah[3], al[3]);
-      // B fragments of the received rows: x[k][n] = Y[n] float 2*b0 + k
-      const int kf = 2 * kb + t;  // float offset of k = t within this block row
-      const bool k0ok = kf < 2 * bb;
-      const bool k1ok = kf + 4 < 2 * bb;
-      const float y00 = (sym0 && k0ok) ? y0[kf] : 0.0f;
-      const float y01 = (sym0 && k1ok) ? y0[kf + 4] : 0.0f;
-      const float y10 = (sym1 && k0ok) ? y1[kf] : 0.0f;
-      const float y11 = (sym1 && k1ok) ? y1[kf + 4] : 0.0f;
-      uint32_t bh00, bl00, bh01, bl01, bh10, bl10, bh11, bl11;
-      split_tf32(y00, bh00, bl00);
-      split_tf32(y01, bh01, bl01);
-      split_tf32(y10, bh10, bl10);
-      split_tf32(y11, bh11, bl11);
-      mma3_tf32(acc[0], ah, al, bh00, bh01, bl00, bl01);
-      mma3_tf32(acc[1], ah, al, bh10, bh11, bl10, bl11);
-      // G: the B column j = gq is h_j, whose (k, j) entries are exactly this
-      // lane's A entries of rows 0-7: b0 = a0, b1 = a2.
-      if (first) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
     }
     __syncwarp();
     if (blk != nblk - 1) continue;
