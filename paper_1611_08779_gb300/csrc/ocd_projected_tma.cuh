@@ -35,10 +35,10 @@ constexpr int kTmaWaitLimit = 1 << 22;  // try_wait polls before a wait is decla
 // Per-warp geometry of the bulk-copy kernel (users padded to 8: the MMA tile
 // has 16 rows = real and imaginary parts of 8 users).
 #ifndef OCD_TMA_BLOCK
-#define OCD_TMA_BLOCK 64      // antennas per staged block
+#define OCD_TMA_BLOCK 32      // antennas per staged block
 #endif
 #ifndef OCD_TMA_MIN_CTAS
-#define OCD_TMA_MIN_CTAS 2    // resident CTAs per SM the register budget targets
+#define OCD_TMA_MIN_CTAS 3    // resident CTAs per SM the register budget targets
 #endif
 #ifndef OCD_TMA_STAGES
 #define OCD_TMA_STAGES 2      // staging buffers per warp (steps in flight + 1)
@@ -140,12 +140,15 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-__device__ __forceinline__ void mma3_tf32(float (&d)[4], const uint32_t (&ah)[4],
+// The three split products go to three accumulators (d[0] = hi*hi,
+// d[1] = hi*lo, d[2] = lo*hi), so consecutive MMAs of one k-step do not wait
+// on each other; they are summed once per pass.
+__device__ __forceinline__ void mma3_tf32(float (&d)[3][4], const uint32_t (&ah)[4],
                                           const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
                                           uint32_t bl0, uint32_t bl1) {
-  mma_tf32(d, al, bh0, bh1);
-  mma_tf32(d, ah, bl0, bl1);
-  mma_tf32(d, ah, bh0, bh1);
+  mma_tf32(d[0], ah, bh0, bh1);
+  mma_tf32(d[1], ah, bl0, bl1);
+  mma_tf32(d[2], al, bh0, bh1);
 }
 
 // ymap: Y viewed as a 2-D float tensor [Nsc*T rows][2B floats], box 32 x 16
@@ -183,6 +186,7 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
   if (nsteps == 0) return;
 
   if (lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ymap)) : "memory");
     for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
     fence_mbar_init();
   }
@@ -215,9 +219,10 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     }
   };
 
-  // Accumulator tiles: [0], [1] = q0 for pass symbols 0-7, 8-15; [2] = G.
-  // Rows 0-7 hold real parts and rows 8-15 imaginary parts of user gq.
-  float acc[3][4];
+  // Accumulator tiles: [0], [1] = q0 for pass symbols 0-7, 8-15; [2] = G;
+  // each with its three split-product parts.  Rows 0-7 hold real parts and
+  // rows 8-15 imaginary parts of user gq.
+  float acc[3][3][4];
   uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
 
   // prologue: the first kStages - 1 steps in flight
@@ -259,7 +264,9 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
 #pragma unroll
       for (int n = 0; n < 3; ++n)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[n][e] = 0.0f;
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[n][q][e] = 0.0f;
     }
 
     // ---------------- products on the tensor cores ------------------------
@@ -316,21 +323,27 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
 
     // ---------------- epilogue of a pass ----------------------------------
     // (1) fragments -> shared memory.  Lane (gq, t) holds rows gq (real) and
-    // gq + 8 (imaginary) of columns 2t, 2t + 1 of each tile.
+    // gq + 8 (imaginary) of columns 2t, 2t + 1 of each tile; the split parts
+    // are summed smallest first.
+    float sum[3][4];
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) sum[n][e] = (acc[n][2][e] + acc[n][1][e]) + acc[n][0][e];
 #pragma unroll
     for (int n = 0; n < 2; ++n)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int ts = 8 * n + 2 * t + e;
-        sq[2 * (ts * NU + gq)] = acc[n][e];
-        sq[2 * (ts * NU + gq) + 1] = acc[n][2 + e];
+        sq[2 * (ts * NU + gq)] = sum[n][e];
+        sq[2 * (ts * NU + gq) + 1] = sum[n][2 + e];
       }
     if (first) {
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int j = 2 * t + e;
-        sg[2 * (gq * NU + j)] = acc[2][e];
-        sg[2 * (gq * NU + j) + 1] = acc[2][2 + e];
+        sg[2 * (gq * NU + j)] = sum[2][e];
+        sg[2 * (gq * NU + j) + 1] = sum[2][2 + e];
       }
     }
     __syncwarp();
