@@ -192,29 +192,38 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
   }
   __syncwarp();
 
-  // Issue the copies of step s into buffer `buf`.
-  auto issue = [&](long long s, int buf) {
-    const long long scl = s / steps_per_sc;
-    const int rem = (int)(s - scl * steps_per_sc);
-    const int pass = rem / nblk;
-    const int blk = rem - pass * nblk;
-    const long long sc = gw + scl * nW;
-    const int b0 = blk * BB;
+  // Step cursor: (subcarrier, pass, block) advanced incrementally, so no
+  // step needs an integer division.
+  struct Cursor {
+    long long sc;
+    int pass, blk;
+  };
+  auto advance = [&](Cursor& q) {
+    if (++q.blk == nblk) {
+      q.blk = 0;
+      if (++q.pass == npasses) {
+        q.pass = 0;
+        q.sc += nW;
+      }
+    }
+  };
+
+  // Issue the copies of the step at cursor q into buffer `buf`.
+  auto issue = [&](const Cursor& q, int buf) {
+    const int b0 = q.blk * BB;
     const int bb = min(BB, B - b0);
-    const int tb = pass * S::kPass;
-    const int np = min(S::kPass, T - tb);
+    const int tb = q.pass * S::kPass;
     const uint32_t bar = bar0 + 8 * buf;
     unsigned char* bp = ws + buf * S::kBufBytes;
     const int nbox = (bb + S::kBoxAnt - 1) / S::kBoxAnt;
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nbox * S::kBoxBytes + bb * U * 8));
     __syncwarp();
     fence_proxy_async();
-    (void)np;
     if (lane < nbox)
       tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), &ymap, 2 * (b0 + S::kBoxAnt * lane),
-                  (int)(sc * T + tb), bar);
+                  (int)(q.sc * T + tb), bar);
     if (lane == 31) {
-      const float2* src = P.H + (sc * (long long)B + b0) * U;
+      const float2* src = P.H + (q.sc * (long long)B + b0) * U;
       bulk_g2s(smem_addr(bp + S::kYBytes), src, (uint32_t)(bb * U * 8), bar);
     }
   };
@@ -226,20 +235,26 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
   uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
 
   // prologue: the first kStages - 1 steps in flight
-  for (int i = 0; i < S::kStages - 1 && i < nsteps; ++i) issue(i, i);
+  Cursor cur{gw, 0, 0};   // step being computed
+  Cursor nxt{gw, 0, 0};   // next step to issue
+  int buf = 0, ibuf = 0;  // buffer of the current step, of the next issue
+  for (int i = 0; i < S::kStages - 1 && i < nsteps; ++i) {
+    issue(nxt, ibuf);
+    advance(nxt);
+    ibuf = ibuf + 1 == S::kStages ? 0 : ibuf + 1;
+  }
   for (long long s = 0; s < nsteps; ++s) {
-    const int buf = (int)(s % S::kStages);
-    {
-      const long long ahead = s + S::kStages - 1;
-      if (ahead < nsteps) issue(ahead, (int)(ahead % S::kStages));
+    if (s + S::kStages - 1 < nsteps) {
+      issue(nxt, ibuf);
+      advance(nxt);
+      ibuf = ibuf + 1 == S::kStages ? 0 : ibuf + 1;
     }
     if (!mbar_wait(bar0 + 8 * buf, (parity >> buf) & 1)) {
       if (lane == 0) atomicOr(&g_tma_fault, 1u);
       // let the copies already in flight finish (bounded) before leaving
       for (int i = 1; i < S::kStages; ++i) {
-        const long long sp = s + i;
-        if (sp < nsteps) {
-          const int bi = (int)(sp % S::kStages);
+        if (s + i < nsteps) {
+          const int bi = (buf + i) % S::kStages;
           mbar_wait(bar0 + 8 * bi, (parity >> bi) & 1);
         }
       }
@@ -247,17 +262,18 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     }
     parity ^= 1u << buf;
 
-    const long long scl = s / steps_per_sc;
-    const int rem = (int)(s - scl * steps_per_sc);
-    const int pass = rem / nblk;
-    const int blk = rem - pass * nblk;
-    const long long sc = gw + scl * nW;
+    const long long sc = cur.sc;
+    const int pass = cur.pass;
+    const int blk = cur.blk;
     const int b0 = blk * BB;
     const int bb = min(BB, B - b0);
     const int tb = pass * S::kPass;
     const int np = min(S::kPass, T - tb);
     const bool first = pass == 0;
-    const unsigned char* bp = ws + buf * S::kBufBytes;
+    const int this_buf = buf;
+    advance(cur);
+    buf = buf + 1 == S::kStages ? 0 : buf + 1;
+    const unsigned char* bp = ws + this_buf * S::kBufBytes;
     const float2* sH = reinterpret_cast<const float2*>(bp + S::kYBytes);
 
     if (blk == 0) {
@@ -376,17 +392,21 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
         zr[l] = 0.0f;
         zi[l] = 0.0f;
       }
+      float dv[NU], pv[NU];
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        dv[u] = spre[4 * u];
+        pv[u] = spre[4 * u + 1];
+      }
       for (int k = 0; k < P.K; ++k) {
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
           if (u < U) {
             const int lu = u % UP;  // compile-time slot of user u
             const int oh = u / UP;  // half that owns user u
-            const float dinv = spre[4 * u];
-            const float pu = spre[4 * u + 1];
             // z_u <- proj(d_u^-1 q_u + p_u z_u) on the owning lane
-            float wr = fmaf(dinv, qr[lu], pu * zr[lu]);
-            float wi = fmaf(dinv, qi[lu], pu * zi[lu]);
+            float wr = fmaf(dv[u], qr[lu], pv[u] * zr[lu]);
+            float wi = fmaf(dv[u], qi[lu], pv[u] * zi[lu]);
             project(wr, wi, P);
             float dr = wr - zr[lu];
             float di = wi - zi[lu];
