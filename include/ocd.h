@@ -124,11 +124,20 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T,
 
 /*
  * ocd_fault_status -- fault word of the kernels that wait on copy engines
- * (bit 0: a bounded wait for a bulk copy expired; the affected subcarriers
- * were left unwritten).  Returns the bits (>= 0) or OCD_ERR_CUDA, and clears
- * them when `clear` is non-zero.  Synchronizes with the current device.
+ * (bit 0: a wait for a bulk copy exceeded its 1 s limit; the affected
+ * subcarriers were left unwritten).  Returns the bits (>= 0) or
+ * OCD_ERR_CUDA, and clears them when `clear` is non-zero.  Synchronizes with
+ * the current device.
  */
 int ocd_fault_status(int clear);
+
+/*
+ * ocd_wait_selftest -- exercises that timeout path: enqueues one warp that
+ * waits, with the same bounded wait, on a barrier nothing ever completes;
+ * after limit_us microseconds (1..2000000) the wait gives up and sets bit 0
+ * of the fault word.  No input or output buffer is involved.
+ */
+int ocd_wait_selftest(int limit_us, cudaStream_t stream);
 
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* ocd_last_error(void);

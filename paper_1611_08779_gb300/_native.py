@@ -40,6 +40,7 @@ SIGNATURES = {
     "ocd_detect_host": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp,
                              _vp, _vp, _vp, _vp, _i, _vp]),
     "ocd_fault_status": (_i, [_i]),
+    "ocd_wait_selftest": (_i, [_i, _vp]),
     "ocd_last_error": (ctypes.c_char_p, []),
     "ocd_version": (_i, []),
 }

@@ -18,6 +18,7 @@ namespace {
 constexpr int kVersion = 100;  // 0.1.0
 constexpr int kMaxDevices = 64;
 constexpr size_t kSmemBudget = 72 * 1024;  // preferred per-CTA budget: >= 3 CTAs per SM
+constexpr unsigned long long kCopyWaitNs = 1000000000ull;  // 1 s limit on any copy wait
 
 thread_local char g_err[512] = "";
 
@@ -244,6 +245,7 @@ int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, fl
   P.rho_scale = N0 > 0.0f ? (float)((double)Es / (double)N0) : 0.0f;
   P.lvl_step = (float)al.step;
   P.vec_y = (B % 2 == 0) && (((uintptr_t)Y & 15u) == 0);
+  P.wait_ns = kCopyWaitNs;
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -397,6 +399,14 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
     e = cudaStreamWaitEvent(stream, hs->ev_out[i], 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
   }
+  return OCD_OK;
+}
+
+int ocd_wait_selftest(int limit_us, cudaStream_t stream) {
+  if (limit_us < 1 || limit_us > 2000000)
+    return fail(OCD_ERR_ARG, "limit_us=%d outside 1..2000000", limit_us);
+  cudaError_t e = ocd::projected_tma_wait_selftest(1000ull * (unsigned long long)limit_us, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
   return OCD_OK;
 }
 

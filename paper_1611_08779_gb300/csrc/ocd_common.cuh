@@ -33,6 +33,7 @@ struct DetectParams {
   int chunk;        // consecutive items per CTA pass (= teams per CTA)
   int scmax;        // largest number of subcarriers a chunk can touch
   int vec_y;        // Y rows may be read with 16-byte loads
+  unsigned long long wait_ns;  // limit of any wait for a copy engine (ns)
 };
 
 using KernelFn = void (*)(DetectParams);
@@ -55,6 +56,10 @@ cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStrea
 // Reads (and optionally clears) the fault word of the bulk-copy kernels;
 // synchronous with respect to the device.
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear);
+// Launches one warp that waits, with the same bounded wait the bulk-copy
+// kernels use, on an mbarrier phase nothing completes; the wait expires
+// after wait_ns and sets the fault word.  Exercises the timeout path.
+cudaError_t projected_tma_wait_selftest(unsigned long long wait_ns, cudaStream_t stream);
 
 // Projection onto C_O (Eq. 14): for square QAM clip real and imaginary parts
 // independently to [-a, a]; for BPSK clip the real part and zero the

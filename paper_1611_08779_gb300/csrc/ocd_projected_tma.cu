@@ -61,4 +61,9 @@ cudaError_t projected_tma_fault(unsigned int* bits, bool clear) {
   return e;
 }
 
+cudaError_t projected_tma_wait_selftest(unsigned long long wait_ns, cudaStream_t stream) {
+  ocd_wait_selftest_kernel<<<1, 32, 0, stream>>>(wait_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace ocd

@@ -30,8 +30,6 @@
 
 namespace ocd {
 
-constexpr int kTmaWaitLimit = 1 << 22;  // try_wait polls before a wait is declared failed
-
 // Per-warp geometry of the bulk-copy kernel (users padded to 8: the MMA tile
 // has 16 rows = real and imaginary parts of 8 users).
 #ifndef OCD_TMA_BLOCK
@@ -110,9 +108,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false after the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < kTmaWaitLimit; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity for at most limit_ns
+// nanoseconds of wall time; false when the limit expires first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (global_ns() - t0 < limit_ns)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -249,13 +256,13 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       advance(nxt);
       ibuf = ibuf + 1 == S::kStages ? 0 : ibuf + 1;
     }
-    if (!mbar_wait(bar0 + 8 * buf, (parity >> buf) & 1)) {
+    if (!mbar_wait(bar0 + 8 * buf, (parity >> buf) & 1, P.wait_ns)) {
       if (lane == 0) atomicOr(&g_tma_fault, 1u);
       // let the copies already in flight finish (bounded) before leaving
       for (int i = 1; i < S::kStages; ++i) {
         if (s + i < nsteps) {
           const int bi = (buf + i) % S::kStages;
-          mbar_wait(bar0 + 8 * bi, (parity >> bi) & 1);
+          mbar_wait(bar0 + 8 * bi, (parity >> bi) & 1, P.wait_ns);
         }
       }
       return;
@@ -458,6 +465,19 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     }
     __syncwarp();
   }
+}
+
+// Timeout self-test: waits on a phase that nothing completes (no copy is
+// ever issued against this barrier), so the bounded wait must expire.
+__global__ void ocd_wait_selftest_kernel(unsigned long long wait_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (!mbar_wait(b, 0, wait_ns) && threadIdx.x == 0) atomicOr(&g_tma_fault, 1u);
 }
 
 }  // namespace ocd
