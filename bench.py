@@ -265,8 +265,8 @@ def run_ours(args):
         # Short timed regions see too few clock samples: keep the same step
         # running (untimed) until the sampling window reaches half a second.
         hold = 0
-        if ms < 1e3 * MIN_CLOCK_WINDOW_S:
-            hold = int((1e3 * MIN_CLOCK_WINDOW_S - ms) / max(ms / args.steps, 1e-3)) + 1
+        if ms < 1e3 * args.clock_window:
+            hold = int((1e3 * args.clock_window - ms) / max(ms / args.steps, 1e-3)) + 1
             with torch.cuda.stream(stream):
                 for _ in range(hold):
                     step()
@@ -341,7 +341,7 @@ def run_ours(args):
         clocks = sampler.summary()
         if clocks is not None:
             clocks["window"] = "timed region" if hold == 0 else \
-                f"timed region + {hold} identical untimed steps (window >= {MIN_CLOCK_WINDOW_S} s)"
+                f"timed region + {hold} identical untimed steps (window >= {args.clock_window} s)"
         alu_peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
         res_launch_s = ms_res / 1e3 / res_steps
         res_tf = 2 * algorithmic_fma_per_sc() * nsc / res_launch_s / 1e12
@@ -396,6 +396,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
+                    help="seconds of clock sampling the timed steps are extended to")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
