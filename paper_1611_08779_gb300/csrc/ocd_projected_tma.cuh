@@ -139,23 +139,25 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   lo = __float_as_uint(x - __uint_as_float(hi));
 }
 // D += A B for one m16n8k8 TF32 tile (A row-major 16x8, B column-major 8x8).
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
+// The A fragment here always has a3 == a0 (Re h in both places), so the
+// register is passed twice.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
-      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      "{%0, %1, %2, %3}, {%4, %5, %6, %4}, {%7, %8}, {%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1));
 }
 // The three split products go to three accumulators (d[0] = hi*hi,
 // d[1] = hi*lo, d[2] = lo*hi), so consecutive MMAs of one k-step do not wait
 // on each other; they are summed once per pass.
-__device__ __forceinline__ void mma3_tf32(float (&d)[3][4], const uint32_t (&ah)[4],
-                                          const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
+__device__ __forceinline__ void mma3_tf32(float (&d)[3][4], const uint32_t (&ah)[3],
+                                          const uint32_t (&al)[3], uint32_t bh0, uint32_t bh1,
                                           uint32_t bl0, uint32_t bl1) {
-  mma_tf32(d[0], ah, bh0, bh1);
-  mma_tf32(d[1], ah, bl0, bl1);
-  mma_tf32(d[2], al, bh0, bh1);
+  mma_tf32(d[0], ah[0], ah[1], ah[2], bh0, bh1);
+  mma_tf32(d[1], ah[0], ah[1], ah[2], bl0, bl1);
+  mma_tf32(d[2], al[0], al[1], al[2], bh0, bh1);
 }
 
 // ymap: Y viewed as a 2-D float tensor [Nsc*T rows][2B floats], box 32 x 16
@@ -183,6 +185,15 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
   // MMA fragment coordinates: row group gq (user / symbol within a tile), thread t
   const int gq = lane >> 2;
   const int t = lane & 3;
+  // Antenna order inside a k-step: {0, 1, 8, 9}[t] + 2 kk (kk = 0..3 within a
+  // 16-antenna box).  Byte offset of this lane's entry in the swizzled box,
+  // row gq (row gq + 8 is 1024 bytes further and has the same swizzle):
+  // chunk (kk | 4 (t >> 1)) lands at chunk ^ gq, half (t & 1).
+  const int ta = ((t >> 1) << 3) | (t & 1);
+  int yoff[4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    yoff[kk] = gq * 128 + (((kk | ((t >> 1) << 2)) ^ gq) << 4) + ((t & 1) << 3);
   const long long nW = (long long)gridDim.x * (blockDim.x >> 5);
   const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
   const int nblk = (B + BB - 1) / BB;
@@ -308,37 +319,48 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     // symbols only reach discarded outputs; antennas beyond B arrive as zeros
     // from the tensor copy, and staged channel rows beyond the block are
     // masked.
-    const bool tail = bb < BB;
-    const int ta = ((t >> 1) << 3) | (t & 1);   // {0, 1, 8, 9}[t]
-    const int r0 = gq, r1 = gq + 8;
-    for (int box = 0; box * S::kBoxAnt < bb; ++box) {
-      const unsigned char* yb = bp + box * S::kBoxBytes;
+    // One k-step: channel pair h (for A) and the two received values.
+    auto kstep = [&](const float2 h, const float2 ya, const float2 yc) {
+      uint32_t ah[3], al[3];
+      split_tf32(h.x, ah[0], al[0]);  // a0 = a3 = Re h
+      split_tf32(h.y, ah[2], al[2]);  // a2 = Im h
+      ah[1] = ah[2] ^ 0x80000000u;    // a1 = -Im h
+      al[1] = al[2] ^ 0x80000000u;
+      uint32_t bh0, bl0, bh1, bl1;
+      split_tf32(ya.x, bh0, bl0);
+      split_tf32(ya.y, bh1, bl1);
+      mma3_tf32(acc[0], ah, al, bh0, bh1, bl0, bl1);
+      split_tf32(yc.x, bh0, bl0);
+      split_tf32(yc.y, bh1, bl1);
+      mma3_tf32(acc[1], ah, al, bh0, bh1, bl0, bl1);
+      // G: the B column j = gq is h_j, whose (k, j) entries are this lane's
+      // A entries of rows 0-7: b0 = a0 = Re, b1 = a2 = Im.
+      if (first) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
+    };
+    const float2* hl = sH + ta * U + gq;  // lane's channel entry, antenna offset ta
+    if (bb == BB) {
+      for (int box = 0; box < S::kBoxes; ++box) {
+        const unsigned char* yb = bp + box * S::kBoxBytes;
 #pragma unroll
-      for (int kb = 0; kb < 8; kb += 2) {
-        const int a = box * S::kBoxAnt + kb + ta;
-        const float2 h = (!tail || a < bb) ? sH[a * U + gq] : make_float2(0.f, 0.f);
-        const int chunk = (kb >> 1) + ((t >> 1) << 2);
-        const float2 ya = *reinterpret_cast<const float2*>(
-            yb + r0 * 128 + ((chunk ^ (r0 & 7)) << 4) + ((t & 1) << 3));
-        const float2 yc = *reinterpret_cast<const float2*>(
-            yb + r1 * 128 + ((chunk ^ (r1 & 7)) << 4) + ((t & 1) << 3));
-        uint32_t ah[4], al[4];
-        split_tf32(h.x, ah[0], al[0]);
-        split_tf32(h.y, ah[2], al[2]);
-        ah[3] = ah[0];
-        al[3] = al[0];
-        ah[1] = ah[2] ^ 0x80000000u;  // -Im h
-        al[1] = al[2] ^ 0x80000000u;
-        uint32_t bh0, bl0, bh1, bl1;
-        split_tf32(ya.x, bh0, bl0);
-        split_tf32(ya.y, bh1, bl1);
-        mma3_tf32(acc[0], ah, al, bh0, bh1, bl0, bl1);
-        split_tf32(yc.x, bh0, bl0);
-        split_tf32(yc.y, bh1, bl1);
-        mma3_tf32(acc[1], ah, al, bh0, bh1, bl0, bl1);
-        // G: the B column j = gq is h_j, whose (k, j) entries are this lane's
-        // A entries of rows 0-7: b0 = a0 = Re, b1 = a2 = Im.
-        if (first) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
+        for (int kk = 0; kk < 4; ++kk) {
+          const float2 h = hl[(box * S::kBoxAnt + 2 * kk) * U];
+          const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+          kstep(h, ya, yc);
+        }
+      }
+    } else {
+      // partial block: channel rows past bb are stale and are masked
+      for (int box = 0; box * S::kBoxAnt < bb; ++box) {
+        const unsigned char* yb = bp + box * S::kBoxBytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int a = box * S::kBoxAnt + 2 * kk + ta;
+          const float2 h = a < bb ? hl[(box * S::kBoxAnt + 2 * kk) * U] : make_float2(0.f, 0.f);
+          const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+          kstep(h, ya, yc);
+        }
       }
     }
     __syncwarp();
@@ -405,30 +427,37 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
         dv[u] = spre[4 * u];
         pv[u] = spre[4 * u + 1];
       }
+      // Projection of Eq. 14 without branches: clip bounds are +inf in MMSE
+      // mode (identity) and 0 on the imaginary axis for BPSK in BOX mode.
+      const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
+      const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
       for (int k = 0; k < P.K; ++k) {
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
           if (u < U) {
             const int lu = u % UP;  // compile-time slot of user u
             const int oh = u / UP;  // half that owns user u
-            // z_u <- proj(d_u^-1 q_u + p_u z_u) on the owning lane
+            // z_u <- proj(d_u^-1 q_u + p_u z_u), dz = z_new - z_old (owner lane)
             float wr = fmaf(dv[u], qr[lu], pv[u] * zr[lu]);
             float wi = fmaf(dv[u], qi[lu], pv[u] * zi[lu]);
-            project(wr, wi, P);
-            float dr = wr - zr[lu];
-            float di = wi - zi[lu];
-            const bool own = hf == oh;
-            if (own) { zr[lu] = wr; zi[lu] = wi; }
-            const float pr = __shfl_xor_sync(kFullMask, dr, 1);
-            const float pi = __shfl_xor_sync(kFullMask, di, 1);
-            if (!own) { dr = pr; di = pi; }
-            // q <- q - G[:, u] dz for my users
+            wr = fminf(fmaxf(wr, -are), are);
+            wi = fminf(fmaxf(wi, -aim), aim);
+            const float dr0 = wr - zr[lu];
+            const float di0 = wi - zi[lu];
+            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+            const int owner = (lane & ~1) | oh;
+            const float dr = __shfl_sync(kFullMask, dr0, owner);
+            const float di = __shfl_sync(kFullMask, di0, owner);
+            // q <- q - G[:, u] dz for my users, with G[j][u] = conj(G[u][j])
+            const float4* gu = reinterpret_cast<const float4*>(sg + 2 * (u * NU + hf * UP));
 #pragma unroll
-            for (int l = 0; l < UP; ++l) {
-              const int j = hf * UP + l;
-              const float2 gju = *reinterpret_cast<const float2*>(sg + 2 * (j * NU + u));
-              qr[l] = fmaf(-gju.x, dr, fmaf(gju.y, di, qr[l]));
-              qi[l] = fmaf(-gju.x, di, fmaf(-gju.y, dr, qi[l]));
+            for (int l2 = 0; l2 < UP / 2; ++l2) {
+              const float4 g2 = gu[l2];
+              const int l = 2 * l2;
+              qr[l] = fmaf(-g2.x, dr, fmaf(-g2.y, di, qr[l]));
+              qi[l] = fmaf(-g2.x, di, fmaf(g2.y, dr, qi[l]));
+              qr[l + 1] = fmaf(-g2.z, dr, fmaf(-g2.w, di, qr[l + 1]));
+              qi[l + 1] = fmaf(-g2.z, di, fmaf(g2.w, dr, qi[l + 1]));
             }
           }
         }
