@@ -26,6 +26,8 @@
 
 #include <cuda.h>  // CUtensorMap (type only; no driver library is linked)
 
+#include <type_traits>
+
 #include "ocd_common.cuh"
 
 namespace ocd {
@@ -171,8 +173,9 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // Align within the shared window by pointer arithmetic on the __shared__
+  // array itself, so every access below stays a shared-memory access.
+  unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   unsigned char* ws = base + warp * S::kWarpBytes;
   float* sq = reinterpret_cast<float*>(ws + S::kOffQ);
   float* sg = reinterpret_cast<float*>(ws + S::kOffG);
@@ -320,7 +323,7 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     // from the tensor copy, and staged channel rows beyond the block are
     // masked.
     // One k-step: channel pair h (for A) and the two received values.
-    auto kstep = [&](const float2 h, const float2 ya, const float2 yc) {
+    auto kstep = [&](const float2 h, const float2 ya, const float2 yc, auto with_g) {
       uint32_t ah[3], al[3];
       split_tf32(h.x, ah[0], al[0]);  // a0 = a3 = Re h
       split_tf32(h.y, ah[2], al[2]);  // a2 = Im h
@@ -335,34 +338,39 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       mma3_tf32(acc[1], ah, al, bh0, bh1, bl0, bl1);
       // G: the B column j = gq is h_j, whose (k, j) entries are this lane's
       // A entries of rows 0-7: b0 = a0 = Re, b1 = a2 = Im.
-      if (first) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
+      if (decltype(with_g)::value) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
     };
     const float2* hl = sH + ta * U + gq;  // lane's channel entry, antenna offset ta
-    if (bb == BB) {
-      for (int box = 0; box < S::kBoxes; ++box) {
-        const unsigned char* yb = bp + box * S::kBoxBytes;
+    auto block = [&](auto with_g) {
+      if (bb == BB) {
+        for (int box = 0; box < S::kBoxes; ++box) {
+          const unsigned char* yb = bp + box * S::kBoxBytes;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const float2 h = hl[(box * S::kBoxAnt + 2 * kk) * U];
-          const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
-          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
-          kstep(h, ya, yc);
+          for (int kk = 0; kk < 4; ++kk) {
+            const float2 h = hl[(box * S::kBoxAnt + 2 * kk) * U];
+            const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+            const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+            kstep(h, ya, yc, with_g);
+          }
+        }
+      } else {
+        // partial block: channel rows past bb are stale and are masked
+        for (int box = 0; box * S::kBoxAnt < bb; ++box) {
+          const unsigned char* yb = bp + box * S::kBoxBytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const int a = box * S::kBoxAnt + 2 * kk + ta;
+            const float2 h =
+                a < bb ? hl[(box * S::kBoxAnt + 2 * kk) * U] : make_float2(0.f, 0.f);
+            const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+            const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+            kstep(h, ya, yc, with_g);
+          }
         }
       }
-    } else {
-      // partial block: channel rows past bb are stale and are masked
-      for (int box = 0; box * S::kBoxAnt < bb; ++box) {
-        const unsigned char* yb = bp + box * S::kBoxBytes;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int a = box * S::kBoxAnt + 2 * kk + ta;
-          const float2 h = a < bb ? hl[(box * S::kBoxAnt + 2 * kk) * U] : make_float2(0.f, 0.f);
-          const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
-          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
-          kstep(h, ya, yc);
-        }
-      }
-    }
+    };
+    if (first) block(std::true_type{});
+    else block(std::false_type{});
     __syncwarp();
     if (blk != nblk - 1) continue;
 
