@@ -55,10 +55,20 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *   OCD_ALGO_PROJECTED  r carried as q = H^H r (U entries per symbol):
  *                       q0 = H^H y and G = H^H H once per subcarrier, then
  *                       h_u^H r = q_u and r -= h_u dz becomes q -= G[:,u] dz.
- *                       Supports U <= 8.
- *   OCD_ALGO_AUTO       PROJECTED when U <= 8 and T >= 2, else RESIDUAL.
+ *                       Supports U <= 8 (float32 storage) or U <= 16 (16-bit
+ *                       storage with B % 4 == 0 and 16-byte aligned H, Y).
+ *   OCD_ALGO_AUTO       PROJECTED when it supports the shape and T >= 2,
+ *                       else RESIDUAL.
  */
 typedef enum { OCD_ALGO_AUTO = 0, OCD_ALGO_RESIDUAL = 1, OCD_ALGO_PROJECTED = 2 } ocd_algo_t;
+
+/*
+ * Storage of H and Y (outputs are always float32): interleaved complex as
+ * float32 pairs (8 bytes), or as bfloat16 / float16 pairs (4 bytes, real part
+ * at the lower address).  The detector computes in float32 on the stored
+ * values: products of 16-bit entries are exact in float32.
+ */
+typedef enum { OCD_STORE_C64 = 0, OCD_STORE_BF16 = 1, OCD_STORE_F16 = 2 } ocd_storage_t;
 
 typedef enum {
   OCD_OK = 0,
@@ -98,11 +108,20 @@ int ocd_detect(const void* H, const void* Y, int Nsc, int B, int U, int T,
 /*
  * ocd_detect_ex -- ocd_detect with an explicit arrangement `algo`
  * (ocd_algo_t).  ocd_detect(...) is ocd_detect_ex(..., OCD_ALGO_AUTO, stream).
- * OCD_ALGO_PROJECTED with U > 8 returns OCD_ERR_UNSUPPORTED.
+ * OCD_ALGO_PROJECTED on a shape it does not support returns OCD_ERR_UNSUPPORTED.
  */
 int ocd_detect_ex(const void* H, const void* Y, int Nsc, int B, int U, int T,
                   float N0, float Es, int K, int mode, int qam_order,
                   void* xhat, float* llr, int algo, cudaStream_t stream);
+
+/*
+ * ocd_detect_typed -- ocd_detect_ex for H and Y in `storage` (ocd_storage_t):
+ * element size 8 bytes (OCD_STORE_C64) or 4 bytes (16-bit pairs), aligned to
+ * the element size.  xhat (complex64) and llr (float32) as above.
+ */
+int ocd_detect_typed(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T,
+                     float N0, float Es, int K, int mode, int qam_order,
+                     void* xhat, float* llr, int algo, cudaStream_t stream);
 
 /*
  * ocd_detect_host -- the same computation on HOST buffers (Eq. 1 inputs in,

@@ -17,6 +17,9 @@ OCD_ERR_UNSUPPORTED = -2
 OCD_ERR_CUDA = -3
 OCD_MMSE = 0
 OCD_BOX = 1
+OCD_STORE_C64 = 0
+OCD_STORE_BF16 = 1
+OCD_STORE_F16 = 2
 OCD_ALGO_AUTO = 0
 OCD_ALGO_RESIDUAL = 1
 OCD_ALGO_PROJECTED = 2
@@ -37,6 +40,8 @@ _f = ctypes.c_float
 SIGNATURES = {
     "ocd_detect": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp, _vp]),
     "ocd_detect_ex": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp, _i, _vp]),
+    "ocd_detect_typed": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp, _i,
+                              _vp]),
     "ocd_detect_host": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp,
                              _vp, _vp, _vp, _vp, _i, _vp]),
     "ocd_fault_status": (_i, [_i]),

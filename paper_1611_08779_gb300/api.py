@@ -34,6 +34,25 @@ def _mode(mode) -> int:
         raise ValueError(f"unknown mode {mode!r}") from None
 
 
+def _storage_of(name, t):
+    """(storage code, logical complex shape) of a channel / received tensor:
+    complex64 -> float32 pairs; complex32 or float16 [..., 2] -> float16
+    pairs; bfloat16 [..., 2] -> bfloat16 pairs."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype == torch.complex64:
+        return _native.OCD_STORE_C64, tuple(t.shape)
+    if t.dtype == torch.complex32:
+        return _native.OCD_STORE_F16, tuple(t.shape)
+    if t.dtype in (torch.bfloat16, torch.float16) and t.dim() >= 1 and t.shape[-1] == 2:
+        code = _native.OCD_STORE_BF16 if t.dtype == torch.bfloat16 else _native.OCD_STORE_F16
+        return code, tuple(t.shape[:-1])
+    raise TypeError(f"{name}: expected complex64, complex32 or a bfloat16/float16 [..., 2] "
+                    f"tensor, got {t.dtype} {tuple(t.shape)}")
+
+
 def _check_c64(name, t, device=None):
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
@@ -57,7 +76,9 @@ def ocd_detect(H: torch.Tensor, Y: torch.Tensor, N0: float, Es: float = 1.0, K: 
                algo: str = "auto", stream: torch.cuda.Stream | None = None):
     """OCD equalization (Algorithm 1) and max-log LLRs (Eq. 9) on the GPU.
 
-    H: complex64 [Nsc, B, U] and Y: complex64 [Nsc, T, B] on one CUDA device.
+    H: [Nsc, B, U] and Y: [Nsc, T, B] complex on one CUDA device, both
+    complex64, or both 16-bit pairs (complex32, or bfloat16 / float16 with a
+    trailing dimension of 2 holding (re, im)).
     `algo` picks the arrangement ("auto", "residual" or "projected"; see
     include/ocd.h).  Returns (xhat complex64 [Nsc, T, U] or None,
     llr float32 [Nsc, T, U, Q] or None).
@@ -65,17 +86,21 @@ def ocd_detect(H: torch.Tensor, Y: torch.Tensor, N0: float, Es: float = 1.0, K: 
     is synchronized.
     """
     lib = _native.load()
-    _check_c64("H", H)
+    storage, hshape = _storage_of("H", H)
+    ystorage, yshape = _storage_of("Y", Y)
     dev = H.device
     if dev.type != "cuda":
         raise ValueError("H must be a CUDA tensor (the detector has no CPU path)")
-    _check_c64("Y", Y, dev)
-    if H.dim() != 3 or Y.dim() != 3:
-        raise ValueError("H must be [Nsc, B, U] and Y [Nsc, T, B]")
-    Nsc, B, U = H.shape
-    T = Y.shape[1]
-    if Y.shape[0] != Nsc or Y.shape[2] != B:
-        raise ValueError(f"Y shape {tuple(Y.shape)} does not match H {tuple(H.shape)}")
+    if Y.device != dev:
+        raise ValueError(f"Y is on {Y.device}, expected {dev}")
+    if ystorage != storage:
+        raise TypeError("H and Y must use the same storage type")
+    if len(hshape) != 3 or len(yshape) != 3:
+        raise ValueError("H must be [Nsc, B, U] and Y [Nsc, T, B] (complex)")
+    Nsc, B, U = hshape
+    T = yshape[1]
+    if yshape[0] != Nsc or yshape[2] != B:
+        raise ValueError(f"Y shape {yshape} does not match H {hshape}")
     Q = bits_per_symbol(qam_order)
     if want_xhat and xhat is None:
         xhat = torch.empty((Nsc, T, U), dtype=torch.complex64, device=dev)
@@ -93,11 +118,11 @@ def ocd_detect(H: torch.Tensor, Y: torch.Tensor, N0: float, Es: float = 1.0, K: 
     if algo not in ALGOS:
         raise ValueError(f"unknown algo {algo!r}")
     with torch.cuda.device(dev):
-        st = lib.ocd_detect_ex(H.data_ptr(), Y.data_ptr(), Nsc, B, U, T, float(N0), float(Es),
-                               int(K), _mode(mode), int(qam_order),
-                               xhat.data_ptr() if xhat is not None else None,
-                               llr.data_ptr() if llr is not None else None,
-                               ALGOS[algo], _stream_handle(stream))
+        st = lib.ocd_detect_typed(H.data_ptr(), Y.data_ptr(), storage, Nsc, B, U, T, float(N0),
+                                  float(Es), int(K), _mode(mode), int(qam_order),
+                                  xhat.data_ptr() if xhat is not None else None,
+                                  llr.data_ptr() if llr is not None else None,
+                                  ALGOS[algo], _stream_handle(stream))
     _native.check(st)
     return xhat, llr
 

@@ -102,6 +102,12 @@ int device_info(int dev, DeviceInfo& out) {
     e = cudaFuncSetAttribute(ocd::projected_tma_kernel_ptr(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    for (int st : {(int)ocd::kStoreBF16, (int)ocd::kStoreF16})
+      for (int u : {8, 16}) {
+        e = cudaFuncSetAttribute(ocd::projected_h16_kernel_ptr(st, u),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -150,11 +156,13 @@ int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl
   }
 }
 
-int validate(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
-             int K, int mode, int qam_order, const void* xhat, const void* llr, int algo,
+int validate(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T, float N0,
+             float Es, int K, int mode, int qam_order, const void* xhat, const void* llr, int algo,
              Alphabet& al) {
   if (algo != OCD_ALGO_AUTO && algo != OCD_ALGO_RESIDUAL && algo != OCD_ALGO_PROJECTED)
     return fail(OCD_ERR_ARG, "unknown algo %d", algo);
+  if (storage != OCD_STORE_C64 && storage != OCD_STORE_BF16 && storage != OCD_STORE_F16)
+    return fail(OCD_ERR_ARG, "unknown storage %d", storage);
   if (Nsc < 0 || T < 0) return fail(OCD_ERR_ARG, "Nsc=%d and T=%d must be >= 0", Nsc, T);
   if (B < 1 || B > OCD_MAX_ANTENNAS) return fail(OCD_ERR_ARG, "B=%d outside 1..%d", B, OCD_MAX_ANTENNAS);
   if (U < 1 || U > OCD_MAX_USERS) return fail(OCD_ERR_ARG, "U=%d outside 1..%d", U, OCD_MAX_USERS);
@@ -168,24 +176,34 @@ int validate(const void* H, const void* Y, int Nsc, int B, int U, int T, float N
   const long long items = (long long)Nsc * T;
   if (items > 0 && !xhat && !llr) return fail(OCD_ERR_ARG, "both outputs are NULL");
   if (items > 0 && (!H || !Y)) return fail(OCD_ERR_ARG, "H and Y must not be NULL");
-  if (((uintptr_t)H | (uintptr_t)Y | (uintptr_t)xhat) & 7u)
-    return fail(OCD_ERR_ARG, "complex arrays must be 8-byte aligned");
+  if ((((uintptr_t)H | (uintptr_t)Y) & (storage == OCD_STORE_C64 ? 7u : 3u)) || ((uintptr_t)xhat & 7u))
+    return fail(OCD_ERR_ARG, "complex arrays must be aligned to their element size");
   if ((uintptr_t)llr & 3u) return fail(OCD_ERR_ARG, "llr must be 4-byte aligned");
   return OCD_OK;
 }
 
-// Algorithm choice for OCD_ALGO_AUTO: the projected form wins whenever its
-// two per-subcarrier products are shared by more than one symbol.
-int resolve_algo(int algo, int U, int T) {
-  if (algo != OCD_ALGO_AUTO) return algo;
-  return (U <= ocd::kProjectedMaxUsers && T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+bool aligned16(const ocd::DetectParams& P) {
+  return ((reinterpret_cast<uintptr_t>(P.H) | reinterpret_cast<uintptr_t>(P.Y)) & 15u) == 0;
+}
+// Bulk-copy variants: float32 storage needs even B (16-byte rows), 16-bit
+// storage B % 4 == 0; both need 16-byte aligned bases.
+bool can_tma32(const ocd::DetectParams& P) {
+  return P.storage == ocd::kStoreC64 && P.U <= ocd::kProjectedMaxUsers && P.B % 2 == 0 &&
+         aligned16(P);
+}
+bool can_h16(const ocd::DetectParams& P) {
+  return P.storage != ocd::kStoreC64 && P.U <= ocd::kH16MaxUsers && P.B % 4 == 0 &&
+         aligned16(P);
+}
+bool can_projected(const ocd::DetectParams& P) {
+  return can_tma32(P) || can_h16(P) || P.U <= ocd::kProjectedMaxUsers;
 }
 
-// The bulk-copy variant streams H and Y through shared memory; it needs
-// 16-byte aligned rows, i.e. even B and 16-byte aligned bases.
-bool tma_eligible(const ocd::DetectParams& P) {
-  return (P.B % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.H) & 15u) == 0) &&
-         ((reinterpret_cast<uintptr_t>(P.Y) & 15u) == 0);
+// Algorithm choice for OCD_ALGO_AUTO: the projected form wins whenever its
+// two per-subcarrier products are shared by more than one symbol.
+int resolve_algo(int algo, const ocd::DetectParams& P) {
+  if (algo != OCD_ALGO_AUTO) return algo;
+  return (can_projected(P) && P.T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
 }
 
 int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
@@ -193,21 +211,26 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   const long long need = (P.Nsc + nt / 32 - 1) / (nt / 32);  // one warp per subcarrier
   int per_sm = 0;
   cudaError_t e;
-  if (tma_eligible(P)) {
-    const size_t smem = ocd::projected_tma_smem_per_cta();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ocd::projected_tma_kernel_ptr(), nt,
-                                                      smem);
+  const bool h16 = can_h16(P);
+  if (can_tma32(P) || h16) {
+    const void* fn = h16 ? ocd::projected_h16_kernel_ptr(P.storage, U) : ocd::projected_tma_kernel_ptr();
+    const size_t smem = h16 ? ocd::projected_h16_smem_per_cta(U) : ocd::projected_tma_smem_per_cta();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm >= 1) {
       long long grid = (long long)di.sms * per_sm;
       if (grid > need) grid = need;
-      e = ocd::launch_projected_tma(P, (unsigned)grid, stream);
+      e = h16 ? ocd::launch_projected_h16(P, (unsigned)grid, stream)
+              : ocd::launch_projected_tma(P, (unsigned)grid, stream);
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e == cudaSuccess) return OCD_OK;
       // no tensor-map encoder in this driver: the load-based variant follows
       if (e != cudaErrorNotSupported) return cuda_fail(e, "projected kernel launch");
     }
   }
+  if (U > ocd::kProjectedMaxUsers)
+    return fail(OCD_ERR_UNSUPPORTED, "projected form for U=%d needs the bulk-copy path "
+                "(16-bit storage, B %% 4 == 0, 16-byte aligned H and Y)", U);
   const int umax = U <= 4 ? 4 : 8;
   KernelFn fn = ocd::projected_kernel(umax);
   const size_t smem = (nt / 32) * ocd::projected_smem_per_warp(umax);
@@ -223,9 +246,9 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   return OCD_OK;
 }
 
-int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
-                  int K, int mode, const Alphabet& al, void* xhat, float* llr, int algo,
-                  cudaStream_t stream) {
+int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T,
+                  float N0, float Es, int K, int mode, const Alphabet& al, void* xhat, float* llr,
+                  int algo, cudaStream_t stream) {
   const long long items = (long long)Nsc * T;
   if (items == 0) return OCD_OK;
   ocd::DetectParams P;
@@ -244,7 +267,8 @@ int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, fl
   P.box_a = (float)(al.radius * sqrt((double)Es));
   P.rho_scale = N0 > 0.0f ? (float)((double)Es / (double)N0) : 0.0f;
   P.lvl_step = (float)al.step;
-  P.vec_y = (B % 2 == 0) && (((uintptr_t)Y & 15u) == 0);
+  P.storage = storage;
+  P.vec_y = (B % 2 == 0) && (((uintptr_t)Y & (storage == ocd::kStoreC64 ? 15u : 7u)) == 0);
   P.wait_ns = kCopyWaitNs;
 
   int dev = 0;
@@ -254,11 +278,11 @@ int launch_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, fl
   int st = device_info(dev, di);
   if (st != OCD_OK) return st;
 
-  algo = resolve_algo(algo, U, T);
+  algo = resolve_algo(algo, P);
   if (algo == OCD_ALGO_PROJECTED) {
-    if (U > ocd::kProjectedMaxUsers)
-      return fail(OCD_ERR_UNSUPPORTED, "projected form supports U <= %d (got %d)",
-                  ocd::kProjectedMaxUsers, U);
+    if (!can_projected(P))
+      return fail(OCD_ERR_UNSUPPORTED, "projected form does not support U=%d with this storage "
+                  "and alignment", U);
     return launch_projected(P, di, U, stream);
   }
 
@@ -317,13 +341,20 @@ int host_streams(int dev, HostStreams*& out) {
 
 extern "C" {
 
+int ocd_detect_typed(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T,
+                     float N0, float Es, int K, int mode, int qam_order, void* xhat, float* llr,
+                     int algo, cudaStream_t stream) {
+  Alphabet al;
+  int st = validate(H, Y, storage, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, algo, al);
+  if (st != OCD_OK) return st;
+  return launch_detect(H, Y, storage, Nsc, B, U, T, N0, Es, K, mode, al, xhat, llr, algo, stream);
+}
+
 int ocd_detect_ex(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
                   int K, int mode, int qam_order, void* xhat, float* llr, int algo,
                   cudaStream_t stream) {
-  Alphabet al;
-  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, algo, al);
-  if (st != OCD_OK) return st;
-  return launch_detect(H, Y, Nsc, B, U, T, N0, Es, K, mode, al, xhat, llr, algo, stream);
+  return ocd_detect_typed(H, Y, OCD_STORE_C64, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat,
+                          llr, algo, stream);
 }
 
 int ocd_detect(const void* H, const void* Y, int Nsc, int B, int U, int T, float N0, float Es,
@@ -336,7 +367,8 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
                     int K, int mode, int qam_order, void* xhat, float* llr, void* dH, void* dY,
                     void* dX, float* dL, int pieces, cudaStream_t stream) {
   Alphabet al;
-  int st = validate(H, Y, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr, OCD_ALGO_AUTO, al);
+  int st = validate(H, Y, OCD_STORE_C64, Nsc, B, U, T, N0, Es, K, mode, qam_order, xhat, llr,
+                    OCD_ALGO_AUTO, al);
   if (st != OCD_OK) return st;
   if (pieces < 1 || pieces > 64) return fail(OCD_ERR_ARG, "pieces=%d outside 1..64", pieces);
   const long long items = (long long)Nsc * T;
@@ -382,7 +414,8 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync Y");
     char* dx = xhat ? static_cast<char*>(dX) + a * xsz : nullptr;
     float* dl = llr ? reinterpret_cast<float*>(reinterpret_cast<char*>(dL) + a * lsz) : nullptr;
-    st = launch_detect(dh, dy, n, B, U, T, N0, Es, K, mode, al, dx, dl, OCD_ALGO_AUTO, s);
+    st = launch_detect(dh, dy, OCD_STORE_C64, n, B, U, T, N0, Es, K, mode, al, dx, dl,
+                       OCD_ALGO_AUTO, s);
     if (st != OCD_OK) return st;
     if (xhat) {
       e = cudaMemcpyAsync(static_cast<char*>(xhat) + a * xsz, dx, n * xsz, cudaMemcpyDeviceToHost, s);
@@ -411,10 +444,11 @@ int ocd_wait_selftest(int limit_us, cudaStream_t stream) {
 }
 
 int ocd_fault_status(int clear) {
-  unsigned int bits = 0;
+  unsigned int bits = 0, bits16 = 0;
   cudaError_t e = ocd::projected_tma_fault(&bits, clear != 0);
+  if (e == cudaSuccess) e = ocd::projected_h16_fault(&bits16, clear != 0);
   if (e != cudaSuccess) return cuda_fail(e, "reading the fault word");
-  return (int)bits;
+  return (int)(bits | bits16);
 }
 
 const char* ocd_last_error(void) { return g_err; }

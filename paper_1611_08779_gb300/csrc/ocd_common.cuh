@@ -2,6 +2,7 @@
 // projection of Eq. 14 and the per-dimension max-log LLR of Eq. 9.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
@@ -11,8 +12,12 @@ namespace ocd {
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kUserSlots = 32;  // per-subcarrier slots of the preprocessing tables
 
+// Storage of H and Y: interleaved complex as float32 pairs (8 bytes) or as
+// bfloat16 / float16 pairs (4 bytes); outputs are always float32.
+enum Storage { kStoreC64 = 0, kStoreBF16 = 1, kStoreF16 = 2 };
+
 struct DetectParams {
-  const float2* __restrict__ H;  // [Nsc][B][U]
+  const float2* __restrict__ H;  // [Nsc][B][U]  (16-bit storage: 4-byte elements)
   const float2* __restrict__ Y;  // [Nsc][T][B]
   float2* __restrict__ xhat;     // [Nsc][T][U] or null
   float* __restrict__ llr;       // [Nsc][T][U][Q] or null
@@ -34,7 +39,28 @@ struct DetectParams {
   int scmax;        // largest number of subcarriers a chunk can touch
   int vec_y;        // Y rows may be read with 16-byte loads
   unsigned long long wait_ns;  // limit of any wait for a copy engine (ns)
+  int storage;      // Storage of H and Y
 };
+
+// Converting loads of complex element `idx` of a [.. ] array in `storage`.
+__device__ __forceinline__ float2 unpack_c16(uint32_t v, int storage) {
+  if (storage == kStoreBF16)  // real part in the low half (lower address)
+    return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+  __half2 h;
+  memcpy(&h, &v, sizeof(h));
+  return __half22float2(h);
+}
+__device__ __forceinline__ float2 load_c(const float2* base, long long idx, int storage) {
+  if (storage == kStoreC64) return __ldg(base + idx);
+  return unpack_c16(__ldg(reinterpret_cast<const uint32_t*>(base) + idx), storage);
+}
+// Two consecutive complex elements idx, idx+1 (idx even, 8/16-byte aligned).
+__device__ __forceinline__ float4 load_c2(const float2* base, long long idx, int storage) {
+  if (storage == kStoreC64) return __ldg(reinterpret_cast<const float4*>(base + idx));
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint32_t*>(base) + idx));
+  const float2 a = unpack_c16(v.x, storage), b = unpack_c16(v.y, storage);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
 
 using KernelFn = void (*)(DetectParams);
 
@@ -56,6 +82,13 @@ cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStrea
 // Reads (and optionally clears) the fault word of the bulk-copy kernels;
 // synchronous with respect to the device.
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear);
+// 16-bit-storage projected kernels (U <= 16): need B % 4 == 0 and 16-byte
+// aligned H, Y.
+constexpr int kH16MaxUsers = 16;
+const void* projected_h16_kernel_ptr(int storage, int U);
+size_t projected_h16_smem_per_cta(int U);
+cudaError_t launch_projected_h16(const DetectParams& P, unsigned grid, cudaStream_t stream);
+cudaError_t projected_h16_fault(unsigned int* bits, bool clear);
 // Launches one warp that waits, with the same bounded wait the bulk-copy
 // kernels use, on an mbarrier phase nothing completes; the wait expires
 // after wait_ns and sets the fault word.  Exercises the timeout path.

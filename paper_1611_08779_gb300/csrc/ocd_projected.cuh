@@ -73,11 +73,12 @@ ocd_projected_kernel(const DetectParams P) {
   const int pairs = (B + 1) >> 1;
   const long long nwarps_total = (long long)gridDim.x * (blockDim.x >> 5);
   const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  const bool vec_h = (U % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.H) & 15u) == 0);
+  const bool vec_h = (U % 2 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(P.H) & (P.storage == kStoreC64 ? 15u : 7u)) == 0);
 
   for (long long sc = gw; sc < P.Nsc; sc += nwarps_total) {
-    const float2* Hs = P.H + sc * (long long)B * U;
-    const float2* Ys = P.Y + sc * (long long)T * B;
+    const long long hbase = sc * (long long)B * U;
+    const long long ybase = sc * (long long)T * B;
 
     for (int tb = 0; tb < T; tb += S::kPass) {
       const bool first = tb == 0;
@@ -99,15 +100,15 @@ ocd_projected_kernel(const DetectParams P) {
         // two channel rows h[b0][.], h[b0+1][.] (zero beyond U or B)
         float2 h0[UMAX], h1[UMAX];
         {
-          const float2* r0 = Hs + (long long)b0 * U;
-          const float2* r1 = r0 + U;
+          const long long r0 = hbase + (long long)b0 * U;
+          const long long r1 = r0 + U;
           if (vec_h) {
 #pragma unroll
             for (int u = 0; u < UMAX; u += 2) {
               float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
               if (u < U) {
-                a = __ldg(reinterpret_cast<const float4*>(r0 + u));
-                if (ok1) b = __ldg(reinterpret_cast<const float4*>(r1 + u));
+                a = load_c2(P.H, r0 + u, P.storage);
+                if (ok1) b = load_c2(P.H, r1 + u, P.storage);
               }
               h0[u] = make_float2(a.x, a.y); h0[u + 1] = make_float2(a.z, a.w);
               h1[u] = make_float2(b.x, b.y); h1[u + 1] = make_float2(b.z, b.w);
@@ -115,8 +116,8 @@ ocd_projected_kernel(const DetectParams P) {
           } else {
 #pragma unroll
             for (int u = 0; u < UMAX; ++u) {
-              h0[u] = u < U ? __ldg(r0 + u) : make_float2(0.f, 0.f);
-              h1[u] = (u < U && ok1) ? __ldg(r1 + u) : make_float2(0.f, 0.f);
+              h0[u] = u < U ? load_c(P.H, r0 + u, P.storage) : make_float2(0.f, 0.f);
+              h1[u] = (u < U && ok1) ? load_c(P.H, r1 + u, P.storage) : make_float2(0.f, 0.f);
             }
           }
         }
@@ -127,13 +128,13 @@ ocd_projected_kernel(const DetectParams P) {
           const int t = tb + c + S::kCG * i;
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           if (t < T) {
-            const float2* yr = Ys + (long long)t * B + b0;
+            const long long yr = ybase + (long long)t * B + b0;
             if (P.vec_y) {
-              v = __ldg(reinterpret_cast<const float4*>(yr));
+              v = load_c2(P.Y, yr, P.storage);
             } else {
-              const float2 a = __ldg(yr);
+              const float2 a = load_c(P.Y, yr, P.storage);
               v.x = a.x; v.y = a.y;
-              if (ok1) { const float2 b = __ldg(yr + 1); v.z = b.x; v.w = b.y; }
+              if (ok1) { const float2 b = load_c(P.Y, yr + 1, P.storage); v.z = b.x; v.w = b.y; }
             }
           }
           yv[i] = v;

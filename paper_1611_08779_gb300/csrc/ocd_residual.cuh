@@ -109,7 +109,7 @@ ocd_residual_kernel(const DetectParams P) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const bool sym_ok = active && (t0 + s < T);
-      const float2* yrow = P.Y + (sc * T + (sym_ok ? t0 + s : 0)) * (long long)B;
+      const long long yrow = (sc * T + (sym_ok ? t0 + s : 0)) * (long long)B;
       const int p0 = lt * NPP;
 #pragma unroll
       for (int j = 0; j < NPP; ++j) {
@@ -117,10 +117,14 @@ ocd_residual_kernel(const DetectParams P) {
         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (sym_ok) {
           if (P.vec_y) {
-            if (b0 < B) v = __ldg(reinterpret_cast<const float4*>(yrow) + p0 + j);
+            if (b0 < B) v = load_c2(P.Y, yrow + b0, P.storage);
           } else {
-            if (b0 < B) { const float2 a = __ldg(yrow + b0); v.x = a.x; v.y = a.y; }
-            if (b0 + 1 < B) { const float2 a = __ldg(yrow + b0 + 1); v.z = a.x; v.w = a.y; }
+            if (b0 < B) { const float2 a = load_c(P.Y, yrow + b0, P.storage); v.x = a.x; v.y = a.y; }
+            if (b0 + 1 < B) {
+              const float2 a = load_c(P.Y, yrow + b0 + 1, P.storage);
+              v.z = a.x;
+              v.w = a.y;
+            }
           }
         }
         r[s][j] = v;
@@ -131,14 +135,14 @@ ocd_residual_kernel(const DetectParams P) {
     // ---- stage H[sc0 .. sc0+nsc) as user-major columns (8 loads in flight) --
     if (stager) {
       for (int s = 0; s < nsc; ++s) {
-        const float2* gH = P.H + (sc0 + s) * (long long)B * U + my_u;
+        const long long gH = (sc0 + s) * (long long)B * U + my_u;
         float2* col = sH + s * lay.sc_stride + my_u * lay.rs;
         for (int b0 = warp * rows + my_r; b0 < B; b0 += 8 * rstep) {
           float2 v[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int b = b0 + q * rstep;
-            if (b < B) v[q] = __ldg(gH + b * U);
+            if (b < B) v[q] = load_c(P.H, gH + (long long)b * U, P.storage);
           }
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
