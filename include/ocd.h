@@ -55,8 +55,9 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *   OCD_ALGO_PROJECTED  r carried as q = H^H r (U entries per symbol):
  *                       q0 = H^H y and G = H^H H once per subcarrier, then
  *                       h_u^H r = q_u and r -= h_u dz becomes q -= G[:,u] dz.
- *                       Supports U <= 8 (float32 storage) or U <= 16 (16-bit
- *                       storage with B % 4 == 0 and 16-byte aligned H, Y).
+ *                       Supports U <= 8 always, and U <= 16 when H and Y
+ *                       are 16-byte aligned with even B (float32 storage)
+ *                       or B % 4 == 0 (16-bit storage).
  *   OCD_ALGO_AUTO       PROJECTED when it supports the shape and T >= 2,
  *                       else RESIDUAL.
  */

@@ -99,9 +99,11 @@ int device_info(int dev, DeviceInfo& out) {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
-    e = cudaFuncSetAttribute(ocd::projected_tma_kernel_ptr(),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    for (int u : {8, 16}) {
+      e = cudaFuncSetAttribute(ocd::projected_tma_kernel_ptr(u),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
     for (int st : {(int)ocd::kStoreBF16, (int)ocd::kStoreF16})
       for (int u : {8, 16}) {
         e = cudaFuncSetAttribute(ocd::projected_h16_kernel_ptr(st, u),
@@ -188,7 +190,7 @@ bool aligned16(const ocd::DetectParams& P) {
 // Bulk-copy variants: float32 storage needs even B (16-byte rows), 16-bit
 // storage B % 4 == 0; both need 16-byte aligned bases.
 bool can_tma32(const ocd::DetectParams& P) {
-  return P.storage == ocd::kStoreC64 && P.U <= ocd::kProjectedMaxUsers && P.B % 2 == 0 &&
+  return P.storage == ocd::kStoreC64 && P.U <= ocd::kTmaMaxUsers && P.B % 2 == 0 &&
          aligned16(P);
 }
 bool can_h16(const ocd::DetectParams& P) {
@@ -213,8 +215,10 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   cudaError_t e;
   const bool h16 = can_h16(P);
   if (can_tma32(P) || h16) {
-    const void* fn = h16 ? ocd::projected_h16_kernel_ptr(P.storage, U) : ocd::projected_tma_kernel_ptr();
-    const size_t smem = h16 ? ocd::projected_h16_smem_per_cta(U) : ocd::projected_tma_smem_per_cta();
+    const void* fn =
+        h16 ? ocd::projected_h16_kernel_ptr(P.storage, U) : ocd::projected_tma_kernel_ptr(U);
+    const size_t smem =
+        h16 ? ocd::projected_h16_smem_per_cta(U) : ocd::projected_tma_smem_per_cta(U);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm >= 1) {
@@ -230,7 +234,7 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   }
   if (U > ocd::kProjectedMaxUsers)
     return fail(OCD_ERR_UNSUPPORTED, "projected form for U=%d needs the bulk-copy path "
-                "(16-bit storage, B %% 4 == 0, 16-byte aligned H and Y)", U);
+                "(even B, or B %% 4 == 0 for 16-bit storage; 16-byte aligned H and Y)", U);
   const int umax = U <= 4 ? 4 : 8;
   KernelFn fn = ocd::projected_kernel(umax);
   const size_t smem = (nt / 32) * ocd::projected_smem_per_warp(umax);

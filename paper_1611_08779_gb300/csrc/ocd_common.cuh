@@ -76,8 +76,9 @@ constexpr int kProjectedMaxUsers = 8;
 // (128 threads per CTA).  launch_projected_tma encodes the tensor map of Y
 // and launches; cudaErrorNotSupported means the driver offers no tensor-map
 // encoder.
-const void* projected_tma_kernel_ptr();
-size_t projected_tma_smem_per_cta();
+constexpr int kTmaMaxUsers = 16;
+const void* projected_tma_kernel_ptr(int U);
+size_t projected_tma_smem_per_cta(int U);
 cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream);
 // Reads (and optionally clears) the fault word of the bulk-copy kernels;
 // synchronous with respect to the device.

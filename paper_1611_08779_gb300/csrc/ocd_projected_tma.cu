@@ -26,11 +26,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-const void* projected_tma_kernel_ptr() {
-  return reinterpret_cast<const void*>(ocd_projected_tma_kernel);
+const void* projected_tma_kernel_ptr(int U) {
+  return U <= 8 ? reinterpret_cast<const void*>(ocd_projected_tma_kernel<1>)
+                : reinterpret_cast<const void*>(ocd_projected_tma_kernel<2>);
 }
 
-size_t projected_tma_smem_per_cta() { return 4 * TmaShape::kWarpBytes + 1024; }
+size_t projected_tma_smem_per_cta(int U) {
+  return 4 * (U <= 8 ? TmaShape<1>::kWarpBytes : TmaShape<2>::kWarpBytes) + 1024;
+}
 
 cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -39,7 +42,7 @@ cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStrea
   CUtensorMap map;
   const cuuint64_t dims[2] = {2ull * (cuuint64_t)P.B, (cuuint64_t)P.Nsc * (cuuint64_t)P.T};
   const cuuint64_t strides[1] = {2ull * (cuuint64_t)P.B * sizeof(float)};
-  const cuuint32_t box[2] = {2 * TmaShape::kBoxAnt, TmaShape::kPass};
+  const cuuint32_t box[2] = {2 * TmaShape<1>::kBoxAnt, TmaShape<1>::kPass};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(P.Y), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -48,8 +51,8 @@ cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStrea
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   DetectParams p = P;
   void* args[] = {&p, &map};
-  return cudaLaunchKernel(projected_tma_kernel_ptr(), dim3(grid), dim3(128), args,
-                          projected_tma_smem_per_cta(), stream);
+  return cudaLaunchKernel(projected_tma_kernel_ptr(P.U), dim3(grid), dim3(128), args,
+                          projected_tma_smem_per_cta(P.U), stream);
 }
 
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear) {

@@ -45,8 +45,11 @@ namespace ocd {
 #define OCD_TMA_STAGES 2      // staging buffers per warp (steps in flight + 1)
 #endif
 
+// Users are padded to 8 * UT: an MMA tile has 16 rows = real and imaginary
+// parts of 8 users, and UT user tiles (1 or 2) cover up to 16 users.
+template <int UT>
 struct TmaShape {
-  static constexpr int kUsers = 8;                          // user slots
+  static constexpr int kUsers = 8 * UT;                     // user slots
   static constexpr int kPass = 16;                          // symbols per pass (2 MMA n-tiles)
   static constexpr int kBB = OCD_TMA_BLOCK;                 // antennas per staged block
   static constexpr int kBoxAnt = 16;                        // antennas per Y box (128 B rows)
@@ -106,9 +109,10 @@ __device__ __forceinline__ void mma3_tf32(float (&d)[3][4], const uint32_t (&ah)
 
 // ymap: Y viewed as a 2-D float tensor [Nsc*T rows][2B floats], box 32 x 16
 // (16 antennas x 16 symbols), 128-byte swizzle, out-of-range elements zero.
-__global__ void __launch_bounds__(128, OCD_TMA_MIN_CTAS)
+template <int UT>
+__global__ void __launch_bounds__(128, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
 ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorMap ymap) {
-  using S = TmaShape;
+  using S = TmaShape<UT>;
   constexpr int BB = S::kBB;
   constexpr int UP = S::kUP;
   constexpr int NU = S::kUsers;
@@ -191,10 +195,13 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     }
   };
 
-  // Accumulator tiles: [0], [1] = q0 for pass symbols 0-7, 8-15; [2] = G;
-  // each with its three split-product parts.  Rows 0-7 hold real parts and
-  // rows 8-15 imaginary parts of user gq.
-  float acc[3][3][4];
+  // Accumulator tiles, each with its three split-product parts: q0 for user
+  // tile m and symbols 0-7 / 8-15 of the pass; G tiles (m, n), n >= m, in the
+  // order (0,0), (0,1), (1,1).  Rows 0-7 hold real parts and rows 8-15
+  // imaginary parts of user m*8 + gq.
+  constexpr int NG = UT == 1 ? 1 : 3;
+  float qacc[UT][2][3][4];
+  float gacc[NG][3][4];
   uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
 
   // prologue: the first kStages - 1 steps in flight
@@ -241,11 +248,19 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
 
     if (blk == 0) {
 #pragma unroll
-      for (int n = 0; n < 3; ++n)
+      for (int m = 0; m < UT; ++m)
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) qacc[m][n][q][e] = 0.0f;
+#pragma unroll
+      for (int n = 0; n < NG; ++n)
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[n][q][e] = 0.0f;
+          for (int e = 0; e < 4; ++e) gacc[n][q][e] = 0.0f;
     }
 
     // ---------------- products on the tensor cores ------------------------
@@ -264,50 +279,54 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     // symbols only reach discarded outputs; antennas beyond B arrive as zeros
     // from the tensor copy, and staged channel rows beyond the block are
     // masked.
-    // One k-step: channel pair h (for A) and the two received values.
-    auto kstep = [&](const float2 h, const float2 ya, const float2 yc, auto with_g) {
-      uint32_t ah[3], al[3];
-      split_tf32(h.x, ah[0], al[0]);  // a0 = a3 = Re h
-      split_tf32(h.y, ah[2], al[2]);  // a2 = Im h
-      ah[1] = ah[2] ^ 0x80000000u;    // a1 = -Im h
-      al[1] = al[2] ^ 0x80000000u;
-      uint32_t bh0, bl0, bh1, bl1;
+    // One k-step: this lane's channel entries h[m] (user m*8 + gq) and the two
+    // received values.
+    const bool mask_u = U < NU;  // last user tile only partly used
+    auto kstep = [&](const float2 (&h)[UT], const float2 ya, const float2 yc, auto with_g) {
+      uint32_t ah[UT][3], al[UT][3];
+#pragma unroll
+      for (int m = 0; m < UT; ++m) {
+        split_tf32(h[m].x, ah[m][0], al[m][0]);  // a0 = a3 = Re h
+        split_tf32(h[m].y, ah[m][2], al[m][2]);  // a2 = Im h
+        ah[m][1] = ah[m][2] ^ 0x80000000u;       // a1 = -Im h
+        al[m][1] = al[m][2] ^ 0x80000000u;
+      }
+      uint32_t bh0, bl0, bh1, bl1, ch0, cl0, ch1, cl1;
       split_tf32(ya.x, bh0, bl0);
       split_tf32(ya.y, bh1, bl1);
-      mma3_tf32(acc[0], ah, al, bh0, bh1, bl0, bl1);
-      split_tf32(yc.x, bh0, bl0);
-      split_tf32(yc.y, bh1, bl1);
-      mma3_tf32(acc[1], ah, al, bh0, bh1, bl0, bl1);
-      // G: the B column j = gq is h_j, whose (k, j) entries are this lane's
-      // A entries of rows 0-7: b0 = a0 = Re, b1 = a2 = Im.
-      if (decltype(with_g)::value) mma3_tf32(acc[2], ah, al, ah[0], ah[2], al[0], al[2]);
+      split_tf32(yc.x, ch0, cl0);
+      split_tf32(yc.y, ch1, cl1);
+#pragma unroll
+      for (int m = 0; m < UT; ++m) {
+        mma3_tf32(qacc[m][0], ah[m], al[m], bh0, bh1, bl0, bl1);
+        mma3_tf32(qacc[m][1], ah[m], al[m], ch0, ch1, cl0, cl1);
+        // G tile (m, n), n >= m: the B column j = n*8 + gq is h_j, i.e. this
+        // lane's A entries of user tile n (b0 = Re, b1 = Im).
+        if (decltype(with_g)::value) {
+#pragma unroll
+          for (int n = m; n < UT; ++n)
+            mma3_tf32(gacc[m == 0 ? n : 2], ah[m], al[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+        }
+      }
     };
     const float2* hl = sH + ta * U + gq;  // lane's channel entry, antenna offset ta
     auto block = [&](auto with_g) {
-      if (bb == BB) {
-        for (int box = 0; box < S::kBoxes; ++box) {
-          const unsigned char* yb = bp + box * S::kBoxBytes;
+      for (int box = 0; box * S::kBoxAnt < bb; ++box) {
+        const unsigned char* yb = bp + box * S::kBoxBytes;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const float2 h = hl[(box * S::kBoxAnt + 2 * kk) * U];
-            const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
-            const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
-            kstep(h, ya, yc, with_g);
-          }
-        }
-      } else {
-        // partial block: channel rows past bb are stale and are masked
-        for (int box = 0; box * S::kBoxAnt < bb; ++box) {
-          const unsigned char* yb = bp + box * S::kBoxBytes;
+        for (int kk = 0; kk < 4; ++kk) {
+          const int a = box * S::kBoxAnt + 2 * kk + ta;
+          // channel rows past bb are stale in the staging buffer: masked
+          const bool ok = bb == BB || a < bb;
+          float2 h[UT];
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const int a = box * S::kBoxAnt + 2 * kk + ta;
-            const float2 h =
-                a < bb ? hl[(box * S::kBoxAnt + 2 * kk) * U] : make_float2(0.f, 0.f);
-            const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
-            const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
-            kstep(h, ya, yc, with_g);
+          for (int m = 0; m < UT; ++m) {
+            const bool okm = ok && !(mask_u && m * 8 + gq >= U);
+            h[m] = okm ? hl[(box * S::kBoxAnt + 2 * kk) * U + m * 8] : make_float2(0.f, 0.f);
           }
+          const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+          kstep(h, ya, yc, with_g);
         }
       }
     };
@@ -320,26 +339,36 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     // (1) fragments -> shared memory.  Lane (gq, t) holds rows gq (real) and
     // gq + 8 (imaginary) of columns 2t, 2t + 1 of each tile; the split parts
     // are summed smallest first.
-    float sum[3][4];
 #pragma unroll
-    for (int n = 0; n < 3; ++n)
+    for (int m = 0; m < UT; ++m)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) sum[n][e] = (acc[n][2][e] + acc[n][1][e]) + acc[n][0][e];
+      for (int n = 0; n < 2; ++n)
 #pragma unroll
-    for (int n = 0; n < 2; ++n)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int ts = 8 * n + 2 * t + e;
-        sq[2 * (ts * NU + gq)] = sum[n][e];
-        sq[2 * (ts * NU + gq) + 1] = sum[n][2 + e];
-      }
+        for (int e = 0; e < 2; ++e) {
+          const int ts = 8 * n + 2 * t + e;
+          const int u = m * 8 + gq;
+          const float (&a)[3][4] = qacc[m][n];
+          sq[2 * (ts * NU + u)] = (a[2][e] + a[1][e]) + a[0][e];
+          sq[2 * (ts * NU + u) + 1] = (a[2][2 + e] + a[1][2 + e]) + a[0][2 + e];
+        }
     if (first) {
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int j = 2 * t + e;
-        sg[2 * (gq * NU + j)] = sum[2][e];
-        sg[2 * (gq * NU + j) + 1] = sum[2][2 + e];
-      }
+      for (int m = 0; m < UT; ++m)
+#pragma unroll
+        for (int n = m; n < UT; ++n)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float (&a)[3][4] = gacc[m == 0 ? n : 2];
+            const float re = (a[2][e] + a[1][e]) + a[0][e];
+            const float im = (a[2][2 + e] + a[1][2 + e]) + a[0][2 + e];
+            const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
+            sg[2 * (i * NU + j)] = re;
+            sg[2 * (i * NU + j) + 1] = im;
+            if (n != m) {  // lower block from Hermitian symmetry
+              sg[2 * (j * NU + i)] = re;
+              sg[2 * (j * NU + i) + 1] = -im;
+            }
+          }
     }
     __syncwarp();
     // (2) preprocessing (Algorithm 1) and soft-output constants

@@ -19,8 +19,12 @@ MODE = {orc.MMSE: "mmse", orc.BOX: "box"}
 ALGOS = ["residual", "projected"]
 
 
-def algos_for(U):
-    return ALGOS if U <= 8 else ["residual"]
+def algos_for(U, B=None):
+    """Arrangements supporting the shape: projected for U <= 8, and for
+    U <= 16 when B is even (the bulk-copy kernel; test arrays are aligned)."""
+    if U <= 8 or (U <= 16 and B is not None and B % 2 == 0):
+        return ALGOS
+    return ["residual"]
 
 
 def run_gpu(d, K, mode, order, Es=1.0, N0=None, want_xhat=True, want_llr=True, algo="auto"):
@@ -37,7 +41,7 @@ def check(Nsc, B, U, T, K, mode, order, snr, seed, Es=1.0, label="", algos=None)
     """Every arrangement that supports the shape must match the oracle."""
     d = synth.make_uplink(Nsc, B, U, T, order, snr, seed, Es=Es)
     out = {}
-    for algo in (algos or algos_for(U)):
+    for algo in (algos or algos_for(U, B)):
         x, L = run_gpu(d, K, mode, order, Es, algo=algo)
         out[algo] = assert_parity(x, L, d["H"], d["Y"], d["N0"], Es, K, mode, order,
                                   f"{label} [{algo}]")
@@ -194,12 +198,21 @@ def test_full_size_sampled_against_oracle(algo):
     assert np.all(np.isfinite(L))
 
 
-def test_projected_rejects_more_than_eight_users():
-    d = synth.make_uplink(2, 32, 9, 2, 16, 10.0, 71)
+@pytest.mark.parametrize("B,U", [(33, 9), (32, 17), (31, 16)])
+def test_projected_rejects_unsupported_shapes(B, U):
+    """More than 16 users, or more than 8 with odd B (no bulk-copy staging)."""
+    d = synth.make_uplink(2, B, U, 2, 16, 10.0, 71)
     with pytest.raises(ocd.OcdError, match="UNSUPPORTED"):
         run_gpu(d, 3, orc.MMSE, 16, algo="projected")
     x, L = run_gpu(d, 3, orc.MMSE, 16, algo="auto")  # falls back to the residual form
     assert_parity(x, L, d["H"], d["Y"], d["N0"], 1.0, 3, orc.MMSE, 16)
+
+
+@pytest.mark.parametrize("U", [9, 12, 16])
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_projected_two_user_tiles(mode, U):
+    """9..16 users (two 8-user MMA tiles) in float32 storage, several passes."""
+    check(7, 96, U, 20, 4, mode, 64, 18.0, 500 + U, label=f"96x{U}", algos=["projected"])
 
 
 @pytest.mark.parametrize("T", [1, 2, 15, 16, 17, 33, 40])
