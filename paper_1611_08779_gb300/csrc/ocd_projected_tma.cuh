@@ -311,17 +311,34 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     };
     const float2* hl = sH + ta * U + gq;  // lane's channel entry, antenna offset ta
     auto block = [&](auto with_g) {
+      if (bb == BB && !mask_u) {
+        // full block, full user tiles: no masking
+        for (int box = 0; box < S::kBoxes; ++box) {
+          const unsigned char* yb = bp + box * S::kBoxBytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            float2 h[UT];
+#pragma unroll
+            for (int m = 0; m < UT; ++m) h[m] = hl[(box * S::kBoxAnt + 2 * kk) * U + m * 8];
+            const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+            const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+            kstep(h, ya, yc, with_g);
+          }
+        }
+        return;
+      }
       for (int box = 0; box * S::kBoxAnt < bb; ++box) {
         const unsigned char* yb = bp + box * S::kBoxBytes;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const int a = box * S::kBoxAnt + 2 * kk + ta;
-          // channel rows past bb are stale in the staging buffer: masked
-          const bool ok = bb == BB || a < bb;
+          // channel rows past bb are stale in the staging buffer, and user
+          // slots past U hold other rows' entries: both masked
+          const bool ok = a < bb;
           float2 h[UT];
 #pragma unroll
           for (int m = 0; m < UT; ++m) {
-            const bool okm = ok && !(mask_u && m * 8 + gq >= U);
+            const bool okm = ok && m * 8 + gq < U;
             h[m] = okm ? hl[(box * S::kBoxAnt + 2 * kk) * U + m * 8] : make_float2(0.f, 0.f);
           }
           const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
