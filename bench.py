@@ -53,6 +53,17 @@ def algorithmic_bytes_per_sc(b=B, u=U, t=T, q=Q):
     return 8 * b * u + 8 * t * b + 8 * t * u + 4 * t * u * q
 
 
+def algorithmic_bytes_per_sc_stored(b, u, t, q, elem):
+    """As algorithmic_bytes_per_sc with H, Y stored at `elem` bytes per complex."""
+    return elem * b * u + elem * t * b + 8 * t * u + 4 * t * u * q
+
+
+def to16(x, dtype):
+    """complex64 tensor -> contiguous [..., 2] tensor of a 16-bit dtype."""
+    import torch
+    return torch.view_as_real(x).to(dtype).contiguous()
+
+
 def algorithmic_fma_per_sc(b=B, u=U, t=T, k=K):
     """Algorithm 1: 8BU real FMAs per (sweep, symbol) (Section III-B: one
     inner product and one scalar-by-vector product), plus 2BU for the norms."""
@@ -302,6 +313,44 @@ def run_ours(args):
         ms_res = float(t.item())
     value_res = bits_per_step * res_steps / (ms_res / 1e3) / 1e9
 
+    # Precision forms: the same batch with H and Y stored as bfloat16 / float16
+    # pairs, timed the same way, and compared with the float32-storage outputs.
+    forms = {}
+    xr = xhat.clone()
+    lr = llr.clone()
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        H16, Y16 = to16(H, dt), to16(Y, dt)
+        x16 = torch.empty_like(xhat)
+        l16 = torch.empty_like(llr)
+
+        def step16():
+            ocd.ocd_detect(H16, Y16, N0, 1.0, K, args.mode, ORDER, xhat=x16, llr=l16, stream=stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                step16()
+        barrier()
+        n16 = max(3, min(args.steps, 200))
+        ev0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(n16):
+                step16()
+        ev1.record(stream)
+        barrier()
+        ms16 = ev0.elapsed_time(ev1) / n16
+        b16 = algorithmic_bytes_per_sc_stored(B, U, T, Q, 4) * nsc
+        agree = float(((l16 > 0) == (lr > 0)).float().mean().item())
+        xerr = float(((x16 - xr).abs().pow(2).sum(-1).sqrt()
+                      / xr.abs().pow(2).sum(-1).sqrt().clamp_min(1e-3 * math.sqrt(U))).max().item())
+        forms[name] = {"value": bits_per_step / world / (ms16 / 1e3) / 1e9, "unit": "Gb/s",
+                       "ms_per_step": ms16,
+                       "hbm_frac": b16 / (ms16 / 1e3) / 1e9 / float(measured_peaks()[0].get(
+                           "hbm_gbs", FALLBACK_HBM_GBS)),
+                       "algorithmic_bytes_per_launch": b16,
+                       "hard_bit_agreement_vs_f32_storage": agree,
+                       "max_xhat_rel_diff_vs_f32_storage": xerr}
+        del H16, Y16, x16, l16
+
     # End to end through the host-buffer entry point: pinned inputs copied in
     # and results copied out inside the timed region.
     Hh = torch.from_numpy(d["H"]).pin_memory()
@@ -364,6 +413,7 @@ def run_ours(args):
                              "unit": "TFLOP/s", "frac": res_tf / alu_peak,
                              "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x "
                                             f"{SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)"}},
+            "precision_forms": forms,
             "e2e": {"value": e2e_value, "unit": "Gb/s",
                     "h2d_bytes_per_step": int(Hh.numel() * 8 + Yh.numel() * 8),
                     "d2h_bytes_per_step": int(xh.numel() * 8 + lh.numel() * 4),
@@ -384,6 +434,76 @@ def run_ours(args):
     return 0
 
 
+def run_precision(args):
+    """256x16, 3300 subcarriers, T = 14, K = 4, 64-QAM with H and Y stored as
+    float32, bfloat16 and float16 pairs: throughput of each (inputs 198 MB in
+    float32 > L2), and per-SNR error against the FP64 oracle evaluated on the
+    unquantized inputs (sampled subcarriers)."""
+    import torch
+
+    import oracle as orc
+    import paper_1611_08779_gb300 as ocd
+    from paper_1611_08779_gb300 import synth
+    b, u, t, k, q, nsc = 256, 16, 14, 4, 6, 3300
+    dev = torch.device("cuda", 0)
+    d = synth.make_uplink(nsc, b, u, t, ORDER, SNR_DB, seed=11)
+    H = torch.from_numpy(d["H"]).to(dev)
+    Y = torch.from_numpy(d["Y"]).to(dev)
+    stores = {"f32": (H, Y, 8), "bf16": (to16(H, torch.bfloat16), to16(Y, torch.bfloat16), 4),
+              "f16": (to16(H, torch.float16), to16(Y, torch.float16), 4)}
+    peak = float(measured_peaks()[0].get("hbm_gbs", FALLBACK_HBM_GBS))
+    out = {}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for name, (h, y, elem) in stores.items():
+        x = torch.empty((nsc, t, u), dtype=torch.complex64, device=dev)
+        llr = torch.empty((nsc, t, u, q), dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            ocd.ocd_detect(h, y, d["N0"], 1.0, k, args.mode, ORDER, xhat=x, llr=llr)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            ocd.ocd_detect(h, y, d["N0"], 1.0, k, args.mode, ORDER, xhat=x, llr=llr)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        nbytes = algorithmic_bytes_per_sc_stored(b, u, t, q, elem) * nsc
+        out[name] = {"value": nsc * t * u * q / (ms / 1e3) / 1e9, "unit": "Gb/s",
+                     "ms_per_step": ms, "hbm_frac": nbytes / (ms / 1e3) / 1e9 / peak}
+    # accuracy per SNR against the FP64 oracle on unquantized inputs
+    per_snr = {}
+    m = orc.BOX if args.mode == "box" else orc.MMSE
+    for snr in range(0, 31, 5):
+        ds = synth.make_uplink(48, b, u, t, ORDER, float(snr), seed=100 + snr, dtype=np.complex128)
+        z_ref, l_ref = orc.ocd_detect(ds["H"], ds["Y"], ds["N0"], 1.0, k, m, ORDER)
+        row = {}
+        for name, dt in (("f32", None), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+            h = torch.from_numpy(ds["H"].astype(np.complex64)).to(dev)
+            y = torch.from_numpy(ds["Y"].astype(np.complex64)).to(dev)
+            if dt is not None:
+                h, y = to16(h, dt), to16(y, dt)
+            x, l = ocd.ocd_detect(h, y, ds["N0"], 1.0, k, args.mode, ORDER)
+            x = x.cpu().numpy()
+            l = l.cpu().numpy()
+            xe = np.max(np.linalg.norm(x - z_ref, axis=-1)
+                        / np.maximum(np.linalg.norm(z_ref, axis=-1), 1e-3 * math.sqrt(u)))
+            le = np.abs(l - l_ref) / np.maximum(np.abs(l_ref), 1.0)
+            row[name] = {"xhat_rel_err_max": float(xe), "llr_rel_err_p99": float(np.quantile(le, 0.99)),
+                         "hard_bit_mismatch_vs_oracle": float(np.mean((l > 0) != (l_ref > 0))),
+                         "ber_vs_sent": float(np.mean((l > 0).astype(np.uint8) != ds["bits"]))}
+        row["oracle_ber_vs_sent"] = float(np.mean((l_ref > 0).astype(np.uint8) != ds["bits"]))
+        per_snr[str(snr)] = row
+    line = {"metric": "detected Gb/s, precision form (256x16, 64-QAM, K=4, T=14)",
+            "workload": "precision", "unit": "Gb/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"OCD-{args.mode.upper()} 256x16 64-QAM K=4 T=14, "
+                                   f"{nsc} subcarriers per step", "B": b, "U": u, "T": t, "K": k},
+            "forms": out, "accuracy_per_snr_db": per_snr,
+            "accuracy_sample": "48 subcarriers x 14 symbols per SNR, FP64 oracle on unquantized inputs"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +516,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["metric", "precision"], default="metric",
+                    help="metric: the headline 128x8 configuration; precision: 256x16 K=4 in "
+                         "float32 / bfloat16 / float16 storage with per-SNR accuracy")
     ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
                     help="seconds of clock sampling the timed steps are extended to")
     args = ap.parse_args(argv)
@@ -403,6 +526,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 
