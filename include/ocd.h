@@ -131,7 +131,7 @@ int ocd_detect_typed(const void* H, const void* Y, int storage, int Nsc, int B, 
  * and copies the results back to xhat / llr on the host.  Pinned host memory
  * is needed for the copies to overlap with compute.  The subcarriers are
  * processed in `pieces` consecutive slices (1..64) so that the copies of one
- * slice overlap the kernel of another; the library uses an internal pair of
+ * slice overlap the kernel of another; the library uses four internal
  * streams per device, ordered after `stream` on entry and before it on exit.
  * A NULL host output skips that output (its device buffer may then be NULL).
  * Nothing is synchronized: the host results are valid once `stream` is.

@@ -313,10 +313,14 @@ int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int
 }
 
 // Internal streams of ocd_detect_host (one pair per device, created once).
+#ifndef OCD_HOST_STREAMS
+#define OCD_HOST_STREAMS 4  // internal streams of the host-buffer path
+#endif
+constexpr int kHostStreams = OCD_HOST_STREAMS;
 struct HostStreams {
   bool ready = false;
-  cudaStream_t s[2];
-  cudaEvent_t ev_in, ev_out[2];
+  cudaStream_t s[kHostStreams];
+  cudaEvent_t ev_in, ev_out[kHostStreams];
 };
 HostStreams g_hs[kMaxDevices];
 std::mutex g_hs_mu;
@@ -327,7 +331,7 @@ int host_streams(int dev, HostStreams*& out) {
   HostStreams& h = g_hs[dev];
   if (!h.ready) {
     cudaError_t e;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kHostStreams; ++i) {
       e = cudaStreamCreateWithFlags(&h.s[i], cudaStreamNonBlocking);
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
       e = cudaEventCreateWithFlags(&h.ev_out[i], cudaEventDisableTiming);
@@ -395,7 +399,7 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
 
   e = cudaEventRecord(hs->ev_in, stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kHostStreams; ++i) {
     e = cudaStreamWaitEvent(hs->s[i], hs->ev_in, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
   }
@@ -409,7 +413,7 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
     const long long b = (long long)Nsc * (p + 1) / pieces;
     const int n = (int)(b - a);
     if (n == 0) continue;
-    cudaStream_t s = hs->s[p & 1];
+    cudaStream_t s = hs->s[p % kHostStreams];
     char* dh = static_cast<char*>(dH) + a * hsz;
     char* dy = static_cast<char*>(dY) + a * ysz;
     e = cudaMemcpyAsync(dh, static_cast<const char*>(H) + a * hsz, n * hsz, cudaMemcpyHostToDevice, s);
@@ -430,7 +434,7 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T, 
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync llr");
     }
   }
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kHostStreams; ++i) {
     e = cudaEventRecord(hs->ev_out[i], hs->s[i]);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     e = cudaStreamWaitEvent(stream, hs->ev_out[i], 0);
