@@ -18,3 +18,4 @@ from .ocd import (  # noqa: F401
     preprocess,
     project,
 )
+from .unfolded import bce_loss, maxlog_llr, unfolded_forward, unfolded_loss_and_grad  # noqa: F401,E402
