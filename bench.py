@@ -503,6 +503,102 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
     return 0
 
+def batched_bound_s(spec, hbm_gbs, fma_tflops):
+    """Roofline time of one cell in the arrangement the batched form gives it:
+    the projected form (U <= 16, T >= 2) is bound by HBM; the residual form by
+    max(HBM, FP32 FMA: 8BU per sweep and symbol, Section III-B)."""
+    b, u, t, k = spec["B"], spec["U"], spec["T"], spec["K"]
+    q = int(round(math.log2(spec["order"])))
+    nbytes = algorithmic_bytes_per_sc(b, u, t, q) * spec["Nsc"]
+    t_hbm = nbytes / (hbm_gbs * 1e9)
+    if u <= 16 and t >= 2:
+        return t_hbm, nbytes
+    t_alu = 2.0 * algorithmic_fma_per_sc(b, u, t, k) * spec["Nsc"] / (fma_tflops * 1e12)
+    return max(t_hbm, t_alu), nbytes
+
+
+def run_batched(args):
+    """Mixed cells in one call: (B, U) in {(32,4), (64,8), (128,16), (256,32)},
+    T in {1, 7, 14}, Nsc uniform in [300, 3300], K in [2, 5], MMSE / BOX,
+    16 / 64-QAM (seeded).  Arms: the plain form (one ocd_detect per cell on one
+    stream), the batched persistent launch with default tiles, and the
+    batched launch with autotuned tiles replayed as a CUDA graph."""
+    import torch
+
+    import paper_1611_08779_gb300 as ocd
+    from paper_1611_08779_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = synth.mixed_cell_specs(args.cells, seed=12)
+    cells, bits = [], 0
+    for s in specs:
+        d = synth.make_uplink(s["Nsc"], s["B"], s["U"], s["T"], s["order"], s["snr_db"], s["seed"])
+        cells.append(ocd.make_cell(torch.from_numpy(d["H"]).to(dev), torch.from_numpy(d["Y"]).to(dev),
+                                   d["N0"], 1.0, s["K"], s["mode"], s["order"]))
+        bits += s["Nsc"] * s["T"] * s["U"] * int(round(math.log2(s["order"])))
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma_tf = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    bound = [batched_bound_s(s, hbm, fma_tf) for s in specs]
+    t_bound = sum(b for b, _ in bound)
+    nbytes = sum(n for _, n in bound)
+    ws = ocd.make_workspace(len(cells), dev)
+
+    def per_cell():
+        for c in cells:
+            ocd.ocd_detect(c.H, c.Y, c.N0, c.Es, c.K, c.mode, c.qam_order, xhat=c.xhat, llr=c.llr)
+
+    def timed(fn, steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps
+
+    steps = max(3, min(args.steps, 200))
+    arms = {}
+    arms["per_cell_launches"] = timed(per_cell, steps)
+    arms["batched_default_tiles"] = timed(lambda: ocd.ocd_detect_batched(cells, workspace=ws), steps)
+    t0 = time.perf_counter()
+    tune = ocd.ocd_autotune_batched(cells, reps=2, workspace=ws)
+    tune_s = time.perf_counter() - t0
+    arms["batched_tuned"] = timed(lambda: ocd.ocd_detect_batched(cells, tune=tune, workspace=ws), steps)
+    graph = ocd.BatchedGraph(cells, tune=tune, workspace=ws)
+    sampler = ClockSampler(dev.index)
+    with sampler:
+        arms["batched_tuned_graph"] = ms = timed(graph.launch, steps)
+    graph.close()
+    clocks = sampler.summary()
+    value = bits / (ms / 1e3) / 1e9
+    line = {
+        "metric": "detected Gb/s, batched form (mixed cells in one persistent launch)",
+        "workload": "batched", "value": value, "unit": "Gb/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic (i.i.d. Rayleigh H, Gray QAM, AWGN)",
+        "config": {"workload": f"{len(cells)} mixed cells, {sum(s['Nsc'] for s in specs)} "
+                               f"subcarriers, {bits} bits per step",
+                   "cells": [{k: s[k] for k in ("B", "U", "T", "Nsc", "K", "mode", "order")}
+                             for s in specs],
+                   "l2": "inputs larger than L2 (no flush)"},
+        "arms_gbps": {k: bits / (v / 1e3) / 1e9 for k, v in arms.items()},
+        "arms_ms": arms,
+        "roofline": {"bound": "mixed (hbm for projected cells, max(hbm, fp32) for residual cells)",
+                     "bound_ms": t_bound * 1e3, "frac": t_bound * 1e3 / ms,
+                     "hbm_achieved_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_peak": hbm,
+                     "fp32_peak_tflops": fma_tf, "peak_source": f"{src} hbm_gbs; FP32 nominal"},
+        "tune": tune.entries, "tune_seconds": tune_s,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -516,9 +612,11 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["metric", "precision"], default="metric",
+    ap.add_argument("--workload", choices=["metric", "precision", "batched"], default="metric",
                     help="metric: the headline 128x8 configuration; precision: 256x16 K=4 in "
-                         "float32 / bfloat16 / float16 storage with per-SNR accuracy")
+                         "float32 / bfloat16 / float16 storage with per-SNR accuracy; batched: "
+                         "mixed cells in one persistent launch")
+    ap.add_argument("--cells", type=int, default=24, help="cells of the batched workload")
     ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
                     help="seconds of clock sampling the timed steps are extended to")
     args = ap.parse_args(argv)
@@ -528,6 +626,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -144,7 +144,8 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T,
 
 /*
  * ocd_fault_status -- fault word of the kernels that wait on copy engines
- * (bit 0: a wait for a bulk copy exceeded its 1 s limit; the affected
+ * (bit 0: a wait for a bulk copy exceeded its 1 s limit; bit 1: a batched
+ * launch found a cell's tensor map misaligned; in both cases the affected
  * subcarriers were left unwritten).  Returns the bits (>= 0) or
  * OCD_ERR_CUDA, and clears them when `clear` is non-zero.  Synchronizes with
  * the current device.
@@ -158,6 +159,94 @@ int ocd_fault_status(int clear);
  * of the fault word.  No input or output buffer is involved.
  */
 int ocd_wait_selftest(int limit_us, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched form.  The paper detects one problem at a time; a base station
+ * serving several cells (sectors, carriers) holds several independent
+ * problems with different B, U, Nsc, T, K, mode and alphabet.  The batched
+ * entry points detect a list of such problems ("cells") with persistent
+ * kernels that draw their work from device ticket counters (atomicAdd only;
+ * no kernel waits on another block).  Each cell's results are those of
+ * ocd_detect_typed with the same arguments in the same arrangement.
+ * ------------------------------------------------------------------------- */
+
+/* One cell: the arguments of ocd_detect_typed.  `algo` (ocd_algo_t):
+ * OCD_ALGO_AUTO takes the tune table's choice for the cell's shape, else the
+ * default (PROJECTED for float32 storage, U <= 16, even B, 16-byte aligned H
+ * and Y, and T >= 2; else RESIDUAL).  The batched PROJECTED form needs
+ * exactly those conditions (OCD_ERR_UNSUPPORTED otherwise). */
+typedef struct {
+  const void* H;
+  const void* Y;
+  void* xhat;
+  float* llr;
+  int storage;
+  int Nsc, B, U, T;
+  float N0, Es;
+  int K, mode, qam_order;
+  int algo;
+} ocd_cell_t;
+
+/* Tile choice for the cells of one shape (B, U, T, storage), as picked by
+ * ocd_autotune_batched.  Zero fields take the defaults. */
+typedef struct {
+  int B, U, T, storage;  /* key */
+  int algo;              /* OCD_ALGO_RESIDUAL or OCD_ALGO_PROJECTED */
+  int symbols_per_item;  /* residual form: symbols per work item, 1 or 2 */
+  int lanes_per_item;    /* residual form: lanes per work item, power of two <= 32 */
+  int sc_per_ticket;     /* projected form: subcarriers per ticket, 1..256 */
+  float time_us;         /* tuning measurement of this choice (informative) */
+} ocd_tune_entry_t;
+
+#define OCD_TUNE_MAX_ENTRIES 64
+typedef struct {
+  int n;  /* entries in use */
+  ocd_tune_entry_t entry[OCD_TUNE_MAX_ENTRIES];
+} ocd_tune_t;
+
+/* Device workspace bytes a batched call over `ncells` cells needs (ticket
+ * counters; a multiple of 256).  ncells < 0 gives 0. */
+size_t ocd_batched_workspace_size(int ncells);
+
+/*
+ * ocd_detect_batched -- detects `ncells` cells (0..OCD_MAX_CELLS) in one
+ * enqueue: a zeroing of the workspace's ticket counters, then one persistent
+ * launch per kernel variant the cells need (at most 32 cells per launch),
+ * on up to four internal streams ordered after `stream` on entry and before
+ * it on exit.  `workspace`: caller-owned device memory of at least
+ * ocd_batched_workspace_size(ncells) bytes, 4-byte aligned, not used by
+ * another call in flight.  `tune` may be NULL.  Cells with Nsc*T == 0 are
+ * skipped.  Argument errors name the offending cell; nothing is enqueued
+ * then.  Stream-capturable.
+ */
+#define OCD_MAX_CELLS 1024
+int ocd_detect_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+                       void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * ocd_autotune_batched -- for every distinct (B, U, T, storage) among the
+ * cells, times the candidate tiles (each arrangement the shape supports;
+ * symbols and lanes per item for the residual form, subcarriers per ticket
+ * for the projected form) on those cells' own buffers, `reps` timed runs
+ * (1..100) after one warm-up, and writes the fastest choice per shape to
+ * `tune` (replacing its contents).  Overwrites the cells' outputs;
+ * synchronizes `stream`.  At most OCD_TUNE_MAX_ENTRIES shapes.
+ */
+int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
+                         size_t workspace_bytes, int reps, ocd_tune_t* tune,
+                         cudaStream_t stream);
+
+/*
+ * CUDA-graph form of ocd_detect_batched: ocd_graph_create_batched captures
+ * one ocd_detect_batched call (cells, tune and workspace bound at creation)
+ * into an executable graph on the current device; ocd_graph_launch replays
+ * it on `stream`; ocd_graph_destroy releases it (NULL is ignored).
+ */
+typedef struct ocd_graph ocd_graph_t;
+int ocd_graph_create_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+                             void* workspace, size_t workspace_bytes, ocd_graph_t** graph);
+int ocd_graph_launch(ocd_graph_t* graph, cudaStream_t stream);
+int ocd_graph_destroy(ocd_graph_t* graph);
 
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* ocd_last_error(void);

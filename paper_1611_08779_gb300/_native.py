@@ -26,6 +26,8 @@ OCD_ALGO_PROJECTED = 2
 OCD_MAX_USERS = 32
 OCD_MAX_ANTENNAS = 512
 OCD_MAX_SWEEPS = 256
+OCD_MAX_CELLS = 1024
+OCD_TUNE_MAX_ENTRIES = 64
 
 _STATUS = {OCD_ERR_ARG: "OCD_ERR_ARG", OCD_ERR_UNSUPPORTED: "OCD_ERR_UNSUPPORTED",
            OCD_ERR_CUDA: "OCD_ERR_CUDA"}
@@ -36,6 +38,27 @@ _lock = threading.Lock()
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _f = ctypes.c_float
+_sz = ctypes.c_size_t
+
+
+class CellT(ctypes.Structure):
+    """ocd_cell_t of include/ocd.h."""
+    _fields_ = [("H", _vp), ("Y", _vp), ("xhat", _vp), ("llr", _vp), ("storage", _i),
+                ("Nsc", _i), ("B", _i), ("U", _i), ("T", _i), ("N0", _f), ("Es", _f),
+                ("K", _i), ("mode", _i), ("qam_order", _i), ("algo", _i)]
+
+
+class TuneEntryT(ctypes.Structure):
+    """ocd_tune_entry_t of include/ocd.h."""
+    _fields_ = [("B", _i), ("U", _i), ("T", _i), ("storage", _i), ("algo", _i),
+                ("symbols_per_item", _i), ("lanes_per_item", _i), ("sc_per_ticket", _i),
+                ("time_us", _f)]
+
+
+class TuneT(ctypes.Structure):
+    """ocd_tune_t of include/ocd.h."""
+    _fields_ = [("n", _i), ("entry", TuneEntryT * 64)]
+
 
 SIGNATURES = {
     "ocd_detect": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp, _vp]),
@@ -44,6 +67,12 @@ SIGNATURES = {
                               _vp]),
     "ocd_detect_host": (_i, [_vp, _vp, _i, _i, _i, _i, _f, _f, _i, _i, _i, _vp, _vp,
                              _vp, _vp, _vp, _vp, _i, _vp]),
+    "ocd_batched_workspace_size": (_sz, [_i]),
+    "ocd_detect_batched": (_i, [_vp, _i, _vp, _vp, _sz, _vp]),
+    "ocd_autotune_batched": (_i, [_vp, _i, _vp, _sz, _i, _vp, _vp]),
+    "ocd_graph_create_batched": (_i, [_vp, _i, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
+    "ocd_graph_launch": (_i, [_vp, _vp]),
+    "ocd_graph_destroy": (_i, [_vp]),
     "ocd_fault_status": (_i, [_i]),
     "ocd_wait_selftest": (_i, [_i, _vp]),
     "ocd_last_error": (ctypes.c_char_p, []),

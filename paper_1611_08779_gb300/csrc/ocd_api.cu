@@ -11,14 +11,12 @@
 
 #include "ocd.h"
 #include "ocd_common.cuh"
+#include "ocd_host.h"
 #include "ocd_residual.cuh"
 
-namespace {
+namespace ocdh {
 
 constexpr int kVersion = 100;  // 0.1.0
-constexpr int kMaxDevices = 64;
-constexpr size_t kSmemBudget = 72 * 1024;  // preferred per-CTA budget: >= 3 CTAs per SM
-constexpr unsigned long long kCopyWaitNs = 1000000000ull;  // 1 s limit on any copy wait
 
 thread_local char g_err[512] = "";
 
@@ -45,12 +43,6 @@ int pow2_ceil(int v) { return 1 << ilog2(v < 1 ? 1 : v); }
 // ---------------------------------------------------------------------------
 // Constellation constants (Section II-A, II-D)
 // ---------------------------------------------------------------------------
-struct Alphabet {
-  int Q, nb, M, bpsk;
-  double step;    // 1/sigma
-  double radius;  // max Re{O} at unit energy
-};
-
 bool alphabet_of(int order, Alphabet& a) {
   switch (order) {
     case 2: a = {1, 1, 2, 1, 1.0, 1.0}; return true;
@@ -71,11 +63,6 @@ bool alphabet_of(int order, Alphabet& a) {
 using ocd::KernelFn;
 constexpr int kNpps[4] = {2, 4, 8, 16};
 
-struct DeviceInfo {
-  bool ready = false;
-  int sms = 0;
-  size_t smem_optin = 0;  // largest dynamic shared memory a CTA may opt into
-};
 DeviceInfo g_dev[kMaxDevices];
 std::mutex g_dev_mu;
 
@@ -110,6 +97,26 @@ int device_info(int dev, DeviceInfo& out) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
       }
+    // the batched residual kernels hold a static ticket slot: dynamic
+    // shared memory up to the opt-in limit minus kBatchStaticSmem
+    for (int S = 1; S <= 2; ++S)
+      for (int npp : kNpps) {
+        const void* fn = reinterpret_cast<const void*>(ocd::batched_residual_kernel(npp, S));
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        if (fa.sharedSizeBytes > kBatchStaticSmem)
+          return fail(OCD_ERR_UNSUPPORTED, "batched kernel holds %zu bytes of static shared memory",
+                      fa.sharedSizeBytes);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)kBatchStaticSmem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      }
+    for (int u : {8, 16}) {
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(ocd::batched_tma_kernel(u)),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -121,21 +128,20 @@ int device_info(int dev, DeviceInfo& out) {
 // ---------------------------------------------------------------------------
 // Launch plan
 // ---------------------------------------------------------------------------
-struct Plan {
-  int npp, S, L, nt;
-  size_t smem;
-};
 
 // Two symbols per item when a subcarrier carries several (each staged h
 // block then feeds two inner products and two residual updates); the fewest
 // lanes per item (fewest shuffles) whose staged channels fit the budget.
-int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl) {
-  const int S = T >= 2 ? 2 : 1;
+// S_req / L_req (0 = default) override the symbols and the lanes per item.
+int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl, int S_req,
+              int L_req) {
+  const int S = S_req ? S_req : (T >= 2 ? 2 : 1);
   const int G = (T + S - 1) / S;
   const int npp_cap = 8;
   const int pairs = (B + 1) / 2;
   int L = 1;
   while (L * npp_cap < pairs) L <<= 1;
+  if (L_req > L) L = L_req;
   int nt = 128;
   for (;;) {
     if (L > 32) return fail(OCD_ERR_UNSUPPORTED, "B=%d does not fit the team layout", B);
@@ -250,18 +256,15 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   return OCD_OK;
 }
 
-int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T,
+void build_params(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T,
                   float N0, float Es, int K, int mode, const Alphabet& al, void* xhat, float* llr,
-                  int algo, cudaStream_t stream) {
-  const long long items = (long long)Nsc * T;
-  if (items == 0) return OCD_OK;
-  ocd::DetectParams P;
+                  ocd::DetectParams& P) {
   memset(&P, 0, sizeof(P));
   P.H = static_cast<const float2*>(H);
   P.Y = static_cast<const float2*>(Y);
   P.xhat = static_cast<float2*>(xhat);
   P.llr = llr;
-  P.items = items;
+  P.items = (long long)Nsc * T;
   P.Nsc = Nsc; P.B = B; P.U = U; P.T = T; P.K = K;
   P.box = mode == OCD_BOX;
   P.bpsk = al.bpsk;
@@ -274,6 +277,15 @@ int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int
   P.storage = storage;
   P.vec_y = (B % 2 == 0) && (((uintptr_t)Y & (storage == ocd::kStoreC64 ? 15u : 7u)) == 0);
   P.wait_ns = kCopyWaitNs;
+}
+
+int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T,
+                  float N0, float Es, int K, int mode, const Alphabet& al, void* xhat, float* llr,
+                  int algo, cudaStream_t stream) {
+  const long long items = (long long)Nsc * T;
+  if (items == 0) return OCD_OK;
+  ocd::DetectParams P;
+  build_params(H, Y, storage, Nsc, B, U, T, N0, Es, K, mode, al, xhat, llr, P);
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -293,8 +305,8 @@ int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int
   // Keep several CTAs per SM when the staged channels allow it; otherwise
   // take up to the whole opt-in shared memory of one CTA.
   Plan pl;
-  st = make_plan(B, U, T, kSmemBudget, P, pl);
-  if (st != OCD_OK) st = make_plan(B, U, T, di.smem_optin, P, pl);
+  st = make_plan(B, U, T, kSmemBudget, P, pl, 0, 0);
+  if (st != OCD_OK) st = make_plan(B, U, T, di.smem_optin, P, pl, 0, 0);
   if (st != OCD_OK) return st;
 
   KernelFn fn = ocd::residual_kernel(pl.npp, pl.S);
@@ -312,16 +324,6 @@ int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int
   return OCD_OK;
 }
 
-// Internal streams of ocd_detect_host (one pair per device, created once).
-#ifndef OCD_HOST_STREAMS
-#define OCD_HOST_STREAMS 4  // internal streams of the host-buffer path
-#endif
-constexpr int kHostStreams = OCD_HOST_STREAMS;
-struct HostStreams {
-  bool ready = false;
-  cudaStream_t s[kHostStreams];
-  cudaEvent_t ev_in, ev_out[kHostStreams];
-};
 HostStreams g_hs[kMaxDevices];
 std::mutex g_hs_mu;
 
@@ -345,7 +347,9 @@ int host_streams(int dev, HostStreams*& out) {
   return OCD_OK;
 }
 
-}  // namespace
+}  // namespace ocdh
+
+using namespace ocdh;
 
 extern "C" {
 

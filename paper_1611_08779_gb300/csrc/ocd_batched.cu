@@ -1,0 +1,508 @@
+// Batched form of the C ABI: several independent detection problems
+// ("cells") drained by persistent kernels through device ticket counters, the
+// tile autotuner, and the CUDA-graph wrapper.  See include/ocd.h.
+//
+// Planning (host, per call): every non-empty cell is assigned an arrangement
+// (residual or bulk-copy projected form) and its tiles -- from the tune table
+// when it has an entry for the cell's (B, U, T, storage), else the defaults
+// of the single-problem path.  Cells that run the same kernel instance form a
+// family; a family is split into launches of at most kBatchCellsPerLaunch
+// cells, each launch with its own ticket counter in the workspace and its
+// cell table passed by value as the kernel parameter.  The launches go to up
+// to four internal streams (heaviest first) so that one family's tail overlaps
+// the next family's blocks.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <vector>
+
+#include "ocd.h"
+#include "ocd_batch.cuh"
+#include "ocd_host.h"
+#include "ocd_residual.cuh"
+
+using namespace ocdh;
+
+namespace {
+
+constexpr int kTmaThreads = 128;
+constexpr int kDefaultStepsPerTicket = 8;  // bulk-copy form: staged steps per ticket
+
+struct CellPlan {
+  int index;              // position in the caller's list
+  int kind;               // 0 residual, 1 bulk-copy projected
+  int npp, S, nt, ut;     // kernel instance
+  size_t smem;
+  ocd::DetectParams P;
+  long long tickets;
+  int sc_per_tick;
+  double work;            // rough cost, orders the launches
+};
+
+const ocd_tune_entry_t* find_tune(const ocd_tune_t* tune, const ocd_cell_t& c) {
+  if (!tune) return nullptr;
+  const int n = std::min(std::max(tune->n, 0), OCD_TUNE_MAX_ENTRIES);
+  for (int i = 0; i < n; ++i) {
+    const ocd_tune_entry_t& e = tune->entry[i];
+    if (e.B == c.B && e.U == c.U && e.T == c.T && e.storage == c.storage) return &e;
+  }
+  return nullptr;
+}
+
+// Arrangement and tiles of one cell.  `force` (a tune entry under trial, or
+// NULL) overrides the tune table.
+int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
+              const ocd_tune_entry_t* force, const DeviceInfo& di, CellPlan& cp) {
+  Alphabet al;
+  int st = validate(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode,
+                    c.qam_order, c.xhat, c.llr, c.algo, al);
+  if (st != OCD_OK) return st;
+  cp.index = index;
+  build_params(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode, al, c.xhat,
+               c.llr, cp.P);
+  const ocd_tune_entry_t* te = force ? force : find_tune(tune, c);
+  const bool tma_ok = can_tma32(cp.P);
+  int algo = c.algo;
+  if (algo == OCD_ALGO_AUTO && te && (te->algo == OCD_ALGO_RESIDUAL || te->algo == OCD_ALGO_PROJECTED))
+    algo = te->algo;
+  if (algo == OCD_ALGO_AUTO) algo = (tma_ok && c.T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  if (algo == OCD_ALGO_PROJECTED && !tma_ok)
+    return fail(OCD_ERR_UNSUPPORTED, "batched projected form needs float32 storage, U <= 16, "
+                "even B and 16-byte aligned H and Y (U=%d B=%d)", c.U, c.B);
+  if (algo == OCD_ALGO_PROJECTED) {
+    cp.kind = 1;
+    cp.ut = c.U <= 8 ? 1 : 2;
+    cp.npp = cp.S = 0;
+    cp.nt = kTmaThreads;
+    cp.smem = ocd::projected_tma_smem_per_cta(c.U);
+    int spt = te && te->sc_per_ticket > 0 ? te->sc_per_ticket : 0;
+    if (spt == 0) {
+      const int steps = ocd::tma_steps_per_sc(c.B, c.T);
+      spt = (kDefaultStepsPerTicket + steps - 1) / steps;
+    }
+    if (spt < 1 || spt > 256) return fail(OCD_ERR_ARG, "sc_per_ticket=%d outside 1..256", spt);
+    cp.sc_per_tick = spt;
+    cp.tickets = (c.Nsc + spt - 1) / spt;
+    cp.work = (double)c.Nsc * (8.0 * c.B * c.U + 8.0 * c.T * c.B + 12.0 * c.T * c.U);
+    return OCD_OK;
+  }
+  cp.kind = 0;
+  cp.ut = 0;
+  int S_req = te ? te->symbols_per_item : 0;
+  int L_req = te ? te->lanes_per_item : 0;
+  if (S_req < 0 || S_req > 2) return fail(OCD_ERR_ARG, "symbols_per_item=%d outside 0..2", S_req);
+  if (L_req < 0 || L_req > 32 || (L_req & (L_req - 1)))
+    return fail(OCD_ERR_ARG, "lanes_per_item=%d is not a power of two <= 32", L_req);
+  if (c.T < 2) S_req = 1;
+  Plan pl;
+  st = make_plan(c.B, c.U, c.T, kSmemBudget, cp.P, pl, S_req, L_req);
+  if (st != OCD_OK)
+    st = make_plan(c.B, c.U, c.T, di.smem_optin - kBatchStaticSmem, cp.P, pl, S_req, L_req);
+  if (st != OCD_OK) return st;
+  cp.npp = pl.npp;
+  cp.S = pl.S;
+  cp.nt = pl.nt;
+  cp.smem = pl.smem;
+  cp.sc_per_tick = 0;
+  cp.tickets = (cp.P.items + cp.P.chunk - 1) / cp.P.chunk;
+  cp.work = (double)c.Nsc * c.T * (8.0 * c.B * c.U * (c.K + 0.25));
+  return OCD_OK;
+}
+
+bool same_family(const CellPlan& a, const CellPlan& b) {
+  return a.kind == b.kind && a.npp == b.npp && a.S == b.S && a.nt == b.nt && a.ut == b.ut;
+}
+
+struct Launch {
+  const void* fn;
+  unsigned grid;
+  int nt;
+  size_t smem;
+  double work;
+  std::unique_ptr<ocd::BatchTable> tab;
+};
+
+// Plans every cell and groups them into launches (heaviest first).
+int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+               const ocd_tune_entry_t* force, const DeviceInfo& di,
+               std::vector<Launch>& launches) {
+  std::vector<CellPlan> plans;
+  plans.reserve(ncells);
+  for (int i = 0; i < ncells; ++i) {
+    const ocd_cell_t& c = cells[i];
+    CellPlan cp;
+    const int st = plan_cell(c, i, tune, force, di, cp);
+    if (st != OCD_OK) {
+      char msg[512];
+      snprintf(msg, sizeof(msg), "%s", ocd_last_error());
+      return fail(st, "cell %d: %s", i, msg);
+    }
+    if ((long long)c.Nsc * c.T == 0) continue;
+    plans.push_back(cp);
+  }
+  // families in order of first appearance; each split into launches
+  std::vector<bool> taken(plans.size(), false);
+  for (size_t i = 0; i < plans.size(); ++i) {
+    if (taken[i]) continue;
+    std::vector<size_t> fam;
+    for (size_t j = i; j < plans.size(); ++j)
+      if (!taken[j] && same_family(plans[i], plans[j])) {
+        fam.push_back(j);
+        taken[j] = true;
+      }
+    for (size_t a = 0; a < fam.size(); a += ocd::kBatchCellsPerLaunch) {
+      const size_t b = std::min(fam.size(), a + (size_t)ocd::kBatchCellsPerLaunch);
+      Launch L;
+      L.tab.reset(new ocd::BatchTable);
+      memset(L.tab.get(), 0, sizeof(ocd::BatchTable));
+      const CellPlan& f = plans[fam[a]];
+      L.fn = f.kind == 1 ? reinterpret_cast<const void*>(ocd::batched_tma_kernel(f.ut == 1 ? 8 : 16))
+                         : reinterpret_cast<const void*>(ocd::batched_residual_kernel(f.npp, f.S));
+      L.nt = f.nt;
+      L.smem = 0;
+      L.work = 0.0;
+      long long tick = 0;
+      for (size_t k = a; k < b; ++k) {
+        const CellPlan& cp = plans[fam[k]];
+        ocd::BatchCell& bc = L.tab->cell[k - a];
+        bc.P = cp.P;
+        if (cp.kind == 1) {
+          const cudaError_t e = ocd::encode_ymap(cp.P, &bc.ymap);
+          if (e == cudaErrorNotSupported)
+            return fail(OCD_ERR_UNSUPPORTED, "cell %d: no tensor-map encoder in this driver", cp.index);
+          if (e != cudaSuccess) return fail(OCD_ERR_CUDA, "cell %d: tensor map encoding failed", cp.index);
+        }
+        tick += cp.tickets;
+        bc.tick_end = tick;
+        bc.sc_per_tick = cp.sc_per_tick;
+        L.smem = std::max(L.smem, cp.smem);
+        L.work += cp.work;
+      }
+      if (tick >= 0xffffffffll) return fail(OCD_ERR_UNSUPPORTED, "too many tickets in one launch");
+      L.tab->total = (unsigned int)tick;
+      L.tab->ncells = (int)(b - a);
+      int per_sm = 0;
+      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.fn, L.nt, L.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      if (per_sm < 1) return fail(OCD_ERR_UNSUPPORTED, "batched kernel cannot be resident (smem %zu)", L.smem);
+      long long grid = (long long)di.sms * per_sm;
+      const long long units = f.kind == 1 ? (tick + L.nt / 32 - 1) / (L.nt / 32) : tick;
+      if (grid > units) grid = units;
+      L.grid = (unsigned)grid;
+      launches.push_back(std::move(L));
+    }
+  }
+  std::stable_sort(launches.begin(), launches.end(),
+                   [](const Launch& x, const Launch& y) { return x.work > y.work; });
+  return OCD_OK;
+}
+
+int check_batch_args(const ocd_cell_t* cells, int ncells, void* workspace, size_t bytes) {
+  if (ncells < 0 || ncells > OCD_MAX_CELLS)
+    return fail(OCD_ERR_ARG, "ncells=%d outside 0..%d", ncells, OCD_MAX_CELLS);
+  if (ncells > 0 && !cells) return fail(OCD_ERR_ARG, "cells must not be NULL");
+  if (ncells > 0 && (!workspace || ((uintptr_t)workspace & 3u)))
+    return fail(OCD_ERR_ARG, "workspace must be a 4-byte aligned device pointer");
+  if (ncells > 0 && bytes < ocd_batched_workspace_size(ncells))
+    return fail(OCD_ERR_ARG, "workspace of %zu bytes is smaller than the %zu needed", bytes,
+                ocd_batched_workspace_size(ncells));
+  // every cell's arguments, before any CUDA call
+  for (int i = 0; i < ncells; ++i) {
+    const ocd_cell_t& c = cells[i];
+    Alphabet al;
+    const int st = validate(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode,
+                            c.qam_order, c.xhat, c.llr, c.algo, al);
+    if (st != OCD_OK) {
+      char msg[512];
+      snprintf(msg, sizeof(msg), "%s", ocd_last_error());
+      return fail(st, "cell %d: %s", i, msg);
+    }
+  }
+  return OCD_OK;
+}
+
+// Enqueues the planned launches: counters zeroed on `stream`, then the
+// launches on the internal streams (or on `stream` when there is one).
+int enqueue(std::vector<Launch>& launches, void* workspace, cudaStream_t stream) {
+  if (launches.empty()) return OCD_OK;
+  unsigned int* counters = static_cast<unsigned int*>(workspace);
+  cudaError_t e = cudaMemsetAsync(counters, 0, launches.size() * sizeof(unsigned int), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (launches.size() == 1) {
+    Launch& L = launches[0];
+    unsigned int* ctr = counters;
+    void* args[] = {L.tab.get(), &ctr};
+    e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+    return OCD_OK;
+  }
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_hs_mu);
+  HostStreams* hs = nullptr;
+  int st = host_streams(dev, hs);
+  if (st != OCD_OK) return st;
+  const int ns = (int)std::min(launches.size(), (size_t)kHostStreams);
+  e = cudaEventRecord(hs->ev_in, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  for (int i = 0; i < ns; ++i) {
+    e = cudaStreamWaitEvent(hs->s[i], hs->ev_in, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  for (size_t i = 0; i < launches.size(); ++i) {
+    Launch& L = launches[i];
+    unsigned int* ctr = counters + i;
+    void* args[] = {L.tab.get(), &ctr};
+    e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, hs->s[i % ns]);
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+  }
+  for (int i = 0; i < ns; ++i) {
+    e = cudaEventRecord(hs->ev_out[i], hs->s[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    e = cudaStreamWaitEvent(stream, hs->ev_out[i], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  }
+  return OCD_OK;
+}
+
+int run_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+              const ocd_tune_entry_t* force, void* workspace, cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  DeviceInfo di;
+  int st = device_info(dev, di);
+  if (st != OCD_OK) return st;
+  std::vector<Launch> launches;
+  st = plan_batch(cells, ncells, tune, force, di, launches);
+  if (st != OCD_OK) return st;
+  st = enqueue(launches, workspace, stream);
+  if (st == OCD_OK) {
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+  }
+  return st;
+}
+
+}  // namespace
+
+struct ocd_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
+
+extern "C" {
+
+size_t ocd_batched_workspace_size(int ncells) {
+  if (ncells <= 0) return 0;
+  const size_t b = (size_t)ncells * sizeof(unsigned int);
+  return (b + 255) / 256 * 256;
+}
+
+int ocd_detect_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+                       void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  int st = check_batch_args(cells, ncells, workspace, workspace_bytes);
+  if (st != OCD_OK || ncells == 0) return st;
+  return run_batch(cells, ncells, tune, nullptr, workspace, stream);
+}
+
+int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
+                         size_t workspace_bytes, int reps, ocd_tune_t* tune,
+                         cudaStream_t stream) {
+  int st = check_batch_args(cells, ncells, workspace, workspace_bytes);
+  if (st != OCD_OK) return st;
+  if (!tune) return fail(OCD_ERR_ARG, "tune must not be NULL");
+  if (reps < 1 || reps > 100) return fail(OCD_ERR_ARG, "reps=%d outside 1..100", reps);
+  // validate everything first, so that a bad cell enqueues nothing
+  {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    DeviceInfo di;
+    st = device_info(dev, di);
+    if (st != OCD_OK) return st;
+    std::vector<Launch> probe;
+    st = plan_batch(cells, ncells, nullptr, nullptr, di, probe);
+    if (st != OCD_OK) return st;
+  }
+  ocd_tune_t out;
+  memset(&out, 0, sizeof(out));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  std::vector<ocd_cell_t> group;
+  std::vector<bool> done(ncells, false);
+  for (int i = 0; i < ncells && st == OCD_OK; ++i) {
+    const ocd_cell_t& c = cells[i];
+    if (done[i] || (long long)c.Nsc * c.T == 0) continue;
+    group.clear();
+    for (int j = i; j < ncells; ++j) {
+      const ocd_cell_t& d = cells[j];
+      if (!done[j] && d.B == c.B && d.U == c.U && d.T == c.T && d.storage == c.storage &&
+          (long long)d.Nsc * d.T > 0) {
+        ocd_cell_t g = d;
+        g.algo = OCD_ALGO_AUTO;  // the candidate decides
+        group.push_back(g);
+        done[j] = true;
+      }
+    }
+    if (out.n >= OCD_TUNE_MAX_ENTRIES) {
+      st = fail(OCD_ERR_UNSUPPORTED, "more than %d distinct shapes", OCD_TUNE_MAX_ENTRIES);
+      break;
+    }
+    // candidates: projected (if the shape takes it) x tickets; residual x S x L
+    std::vector<ocd_tune_entry_t> cand;
+    ocd::DetectParams P;
+    Alphabet al;
+    alphabet_of(c.qam_order, al);
+    build_params(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode, al, c.xhat,
+                 c.llr, P);
+    const ocd_tune_entry_t base = {c.B, c.U, c.T, c.storage, 0, 0, 0, 0, 0.0f};
+    bool tma_all = can_tma32(P);
+    for (const ocd_cell_t& g : group) {
+      ocd::DetectParams Pg;
+      build_params(g.H, g.Y, g.storage, g.Nsc, g.B, g.U, g.T, g.N0, g.Es, g.K, g.mode, al,
+                   g.xhat, g.llr, Pg);
+      tma_all = tma_all && can_tma32(Pg);
+    }
+    if (tma_all && c.T >= 1) {
+      for (int spt : {1, 2, 4, 8, 16, 32}) {
+        ocd_tune_entry_t t = base;
+        t.algo = OCD_ALGO_PROJECTED;
+        t.sc_per_ticket = spt;
+        cand.push_back(t);
+      }
+    }
+    for (int S = 1; S <= (c.T >= 2 ? 2 : 1); ++S) {
+      int L0 = 1;
+      while (L0 * 8 < (c.B + 1) / 2) L0 <<= 1;
+      for (int L = L0; L <= 32 && L <= 4 * L0; L <<= 1) {
+        ocd_tune_entry_t t = base;
+        t.algo = OCD_ALGO_RESIDUAL;
+        t.symbols_per_item = S;
+        t.lanes_per_item = L;
+        cand.push_back(t);
+      }
+    }
+    float best = INFINITY;
+    ocd_tune_entry_t pick = base;
+    for (const ocd_tune_entry_t& t : cand) {
+      const int ng = (int)group.size();
+      int s2 = run_batch(group.data(), ng, nullptr, &t, workspace, stream);  // warm-up
+      if (s2 == OCD_ERR_UNSUPPORTED) continue;  // e.g. the tile does not fit
+      if (s2 != OCD_OK) { st = s2; break; }
+      e = cudaEventRecord(e0, stream);
+      for (int r = 0; r < reps && s2 == OCD_OK && e == cudaSuccess; ++r)
+        s2 = run_batch(group.data(), ng, nullptr, &t, workspace, stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (s2 != OCD_OK) { st = s2; break; }
+      if (e != cudaSuccess) { st = cuda_fail(e, "autotune timing"); break; }
+      float ms = 0.0f;
+      e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { st = cuda_fail(e, "cudaEventElapsedTime"); break; }
+      const float us = 1000.0f * ms / reps;
+      if (us < best) {
+        best = us;
+        pick = t;
+        pick.time_us = us;
+      }
+    }
+    if (st == OCD_OK) {
+      if (!(best < INFINITY)) st = fail(OCD_ERR_UNSUPPORTED, "no tile fits shape B=%d U=%d T=%d", c.B, c.U, c.T);
+      else out.entry[out.n++] = pick;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == OCD_OK) *tune = out;
+  return st;
+}
+
+int ocd_graph_create_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+                             void* workspace, size_t workspace_bytes, ocd_graph_t** graph) {
+  if (!graph) return fail(OCD_ERR_ARG, "graph must not be NULL");
+  *graph = nullptr;
+  int st = check_batch_args(cells, ncells, workspace, workspace_bytes);
+  if (st != OCD_OK) return st;
+  std::unique_ptr<ocd_graph> g(new ocd_graph);
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // per-device state (kernel attributes, internal streams) exists before
+  // the capture starts
+  {
+    DeviceInfo di;
+    st = device_info(g->device, di);
+    if (st != OCD_OK) return st;
+    std::lock_guard<std::mutex> lk(g_hs_mu);
+    HostStreams* hs = nullptr;
+    st = host_streams(g->device, hs);
+    if (st != OCD_OK) return st;
+  }
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  st = ncells > 0 ? run_batch(cells, ncells, tune, nullptr, workspace, cs) : OCD_OK;
+  cudaGraph_t cg = nullptr;
+  e = cudaStreamEndCapture(cs, &cg);
+  cudaStreamDestroy(cs);
+  if (st != OCD_OK) {
+    if (cg) cudaGraphDestroy(cg);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    if (cg) cudaGraphDestroy(cg);
+    return cuda_fail(e, "cudaStreamEndCapture");
+  }
+  g->graph = cg;
+  e = cudaGraphInstantiate(&g->exec, cg, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(cg);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  *graph = g.release();
+  return OCD_OK;
+}
+
+int ocd_graph_launch(ocd_graph_t* graph, cudaStream_t stream) {
+  if (!graph || !graph->exec) return fail(OCD_ERR_ARG, "graph must not be NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != graph->device)
+    return fail(OCD_ERR_ARG, "graph was created on device %d, current device is %d", graph->device, dev);
+  e = cudaGraphLaunch(graph->exec, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return OCD_OK;
+}
+
+int ocd_graph_destroy(ocd_graph_t* graph) {
+  if (!graph) return OCD_OK;
+  cudaError_t e = cudaSuccess;
+  if (graph->exec) e = cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) {
+    const cudaError_t e2 = cudaGraphDestroy(graph->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  delete graph;
+  if (e != cudaSuccess) return cuda_fail(e, "destroying the graph");
+  return OCD_OK;
+}
+
+}  // extern "C"

@@ -35,24 +35,37 @@ size_t projected_tma_smem_per_cta(int U) {
   return 4 * (U <= 8 ? TmaShape<1>::kWarpBytes : TmaShape<2>::kWarpBytes) + 1024;
 }
 
-cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream) {
+cudaError_t encode_ymap(const DetectParams& P, CUtensorMap* map) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   // Y as a 2-D float tensor: rows = (subcarrier, symbol), 2B floats per row.
-  CUtensorMap map;
   const cuuint64_t dims[2] = {2ull * (cuuint64_t)P.B, (cuuint64_t)P.Nsc * (cuuint64_t)P.T};
   const cuuint64_t strides[1] = {2ull * (cuuint64_t)P.B * sizeof(float)};
   const cuuint32_t box[2] = {2 * TmaShape<1>::kBoxAnt, TmaShape<1>::kPass};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(P.Y), dims,
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(P.Y), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream) {
+  CUtensorMap map;
+  const cudaError_t e = encode_ymap(P, &map);
+  if (e != cudaSuccess) return e;
   DetectParams p = P;
   void* args[] = {&p, &map};
   return cudaLaunchKernel(projected_tma_kernel_ptr(P.U), dim3(grid), dim3(128), args,
                           projected_tma_smem_per_cta(P.U), stream);
+}
+
+int tma_steps_per_sc(int B, int T) {
+  return ((B + TmaShape<1>::kBB - 1) / TmaShape<1>::kBB) * ((T + TmaShape<1>::kPass - 1) / TmaShape<1>::kPass);
+}
+
+BatchFn batched_tma_kernel(int U) {
+  return U <= 8 ? ocd_batched_tma_kernel<1> : ocd_batched_tma_kernel<2>;
 }
 
 cudaError_t projected_tma_fault(unsigned int* bits, bool clear) {

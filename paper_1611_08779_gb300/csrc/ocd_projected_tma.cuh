@@ -28,6 +28,7 @@
 
 #include <type_traits>
 
+#include "ocd_batch.cuh"
 #include "ocd_common.cuh"
 #include "ocd_tma_util.cuh"
 
@@ -107,26 +108,26 @@ __device__ __forceinline__ void mma3_tf32(float (&d)[3][4], const uint32_t (&ah)
   mma_tf32(d[2], al[0], al[1], al[2], bh0, bh1);
 }
 
-// ymap: Y viewed as a 2-D float tensor [Nsc*T rows][2B floats], box 32 x 16
-// (16 antennas x 16 symbols), 128-byte swizzle, out-of-range elements zero.
+// One warp's walk over the subcarriers first, first + stride, ... (< end) of
+// one problem P whose received rows are described by ymap (Y viewed as a 2-D
+// float tensor [Nsc*T rows][2B floats], box 32 x 16 = 16 antennas x 16
+// symbols, 128-byte swizzle, out-of-range elements zero).  The warp's
+// staging area ws and its barriers (bar0; phase bits in `parity`) outlive the
+// call: every copy issued here is also waited for here, so consecutive calls
+// may walk different problems.  Returns false when a wait timed out (the
+// fault word is set and the warp must leave).
 template <int UT>
-__global__ void __launch_bounds__(128, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
-ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorMap ymap) {
+__device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMap* ymap,
+                                         unsigned char* ws, uint32_t bar0, uint32_t& parity,
+                                         long long first, long long end, long long stride) {
   using S = TmaShape<UT>;
   constexpr int BB = S::kBB;
   constexpr int UP = S::kUP;
   constexpr int NU = S::kUsers;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  // Align within the shared window by pointer arithmetic on the __shared__
-  // array itself, so every access below stays a shared-memory access.
-  unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-  unsigned char* ws = base + warp * S::kWarpBytes;
   float* sq = reinterpret_cast<float*>(ws + S::kOffQ);
   float* sg = reinterpret_cast<float*>(ws + S::kOffG);
   float* spre = reinterpret_cast<float*>(ws + S::kOffPre);
-  const uint32_t bar0 = smem_addr(ws + S::kOffBar);
 
   const int U = P.U;
   const int B = P.B;
@@ -143,21 +144,12 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk)
     yoff[kk] = gq * 128 + (((kk | ((t >> 1) << 2)) ^ gq) << 4) + ((t & 1) << 3);
-  const long long nW = (long long)gridDim.x * (blockDim.x >> 5);
-  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
   const int nblk = (B + BB - 1) / BB;
   const int npasses = (T + S::kPass - 1) / S::kPass;
   const long long steps_per_sc = (long long)npasses * nblk;
-  const long long my_nsc = gw < P.Nsc ? (P.Nsc - 1 - gw) / nW + 1 : 0;
+  const long long my_nsc = first < end ? (end - 1 - first) / stride + 1 : 0;
   const long long nsteps = my_nsc * steps_per_sc;
-  if (nsteps == 0) return;
-
-  if (lane == 0) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ymap)) : "memory");
-    for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
+  if (nsteps == 0) return true;
 
   // Step cursor: (subcarrier, pass, block) advanced incrementally, so no
   // step needs an integer division.
@@ -170,7 +162,7 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       q.blk = 0;
       if (++q.pass == npasses) {
         q.pass = 0;
-        q.sc += nW;
+        q.sc += stride;
       }
     }
   };
@@ -187,7 +179,7 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     __syncwarp();
     fence_proxy_async();
     if (lane < nbox)
-      tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), &ymap, 2 * (b0 + S::kBoxAnt * lane),
+      tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), ymap, 2 * (b0 + S::kBoxAnt * lane),
                   (int)(q.sc * T + tb), bar);
     if (lane == 31) {
       const float2* src = P.H + (q.sc * (long long)B + b0) * U;
@@ -202,11 +194,10 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
   constexpr int NG = UT == 1 ? 1 : 3;
   float qacc[UT][2][3][4];
   float gacc[NG][3][4];
-  uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
 
   // prologue: the first kStages - 1 steps in flight
-  Cursor cur{gw, 0, 0};   // step being computed
-  Cursor nxt{gw, 0, 0};   // next step to issue
+  Cursor cur{first, 0, 0};   // step being computed
+  Cursor nxt{first, 0, 0};   // next step to issue
   int buf = 0, ibuf = 0;  // buffer of the current step, of the next issue
   for (int i = 0; i < S::kStages - 1 && i < nsteps; ++i) {
     issue(nxt, ibuf);
@@ -228,7 +219,7 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
           mbar_wait(bar0 + 8 * bi, (parity >> bi) & 1, P.wait_ns);
         }
       }
-      return;
+      return false;
     }
     parity ^= 1u << buf;
 
@@ -489,6 +480,81 @@ ocd_projected_tma_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       }
     }
     __syncwarp();
+  }
+  return true;
+}
+
+// Single problem: warp gw of the persistent grid takes subcarriers gw,
+// gw + (warps in the grid), ...
+template <int UT>
+__global__ void __launch_bounds__(128, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
+ocd_projected_tma_kernel(const __grid_constant__ DetectParams P,
+                         const __grid_constant__ CUtensorMap ymap) {
+  using S = TmaShape<UT>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  // Align within the shared window by pointer arithmetic on the __shared__
+  // array itself, so every access below stays a shared-memory access.
+  unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  unsigned char* ws = base + warp * S::kWarpBytes;
+  const uint32_t bar0 = smem_addr(ws + S::kOffBar);
+  const long long nW = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (gw >= P.Nsc) return;
+  if (lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ymap)) : "memory");
+    for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
+  tma_walk<UT>(P, &ymap, ws, bar0, parity, gw, P.Nsc, nW);
+}
+
+// Several problems in one persistent launch: each warp draws tickets from a
+// device counter (one atomicAdd per ticket, no waiting on other warps); a
+// ticket is a run of consecutive subcarriers of one cell.  Tickets of cell c
+// are [tick_end[c-1], tick_end[c]).
+template <int UT>
+__global__ void __launch_bounds__(128, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
+ocd_batched_tma_kernel(const __grid_constant__ BatchTable tab, unsigned int* __restrict__ tickets) {
+  using S = TmaShape<UT>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  unsigned char* ws = base + warp * S::kWarpBytes;
+  const uint32_t bar0 = smem_addr(ws + S::kOffBar);
+  if (lane == 0) {
+    for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  int c = 0, prefetched = -1;
+  for (;;) {
+    unsigned int tk = 0;
+    if (lane == 0) tk = atomicAdd(tickets, 1u);
+    tk = __shfl_sync(kFullMask, tk, 0);
+    if (tk >= tab.total) return;
+    // a warp's tickets increase, so its cell index only moves forward
+    while (tk >= tab.cell[c].tick_end) ++c;
+    const BatchCell& C = tab.cell[c];
+    if (c != prefetched) {
+      // a tensor copy needs a 64-byte aligned map: record and leave otherwise
+      if (reinterpret_cast<uintptr_t>(&C.ymap) & 63u) {
+        if (lane == 0) atomicOr(&g_tma_fault, 2u);
+        return;
+      }
+      if (lane == 0)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&C.ymap)) : "memory");
+      prefetched = c;
+    }
+    const long long t0 = c ? tab.cell[c - 1].tick_end : 0;
+    const long long lo = ((long long)tk - t0) * C.sc_per_tick;
+    const long long hi = min(lo + (long long)C.sc_per_tick, (long long)C.P.Nsc);
+    if (!tma_walk<UT>(C.P, &C.ymap, ws, bar0, parity, lo, hi, 1)) return;
   }
 }
 

@@ -20,4 +20,20 @@ KernelFn residual_kernel(int npp, int s) {
   }
 }
 
+BatchFn batched_residual_kernel(int npp, int s) {
+  if (s == 2) {
+    switch (npp) {
+      case 2: return ocd_batched_residual_kernel<2, 2>;
+      case 4: return ocd_batched_residual_kernel<4, 2>;
+      default: return ocd_batched_residual_kernel<8, 2>;
+    }
+  }
+  switch (npp) {
+    case 2: return ocd_batched_residual_kernel<2, 1>;
+    case 4: return ocd_batched_residual_kernel<4, 1>;
+    case 8: return ocd_batched_residual_kernel<8, 1>;
+    default: return ocd_batched_residual_kernel<16, 1>;
+  }
+}
+
 }  // namespace ocd

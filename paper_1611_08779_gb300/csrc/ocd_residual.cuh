@@ -24,6 +24,7 @@
 // team) so the user loop stays rolled and the sweep body stays small.
 #pragma once
 
+#include "ocd_batch.cuh"
 #include "ocd_common.cuh"
 
 namespace ocd {
@@ -52,10 +53,12 @@ __host__ __device__ inline ResidualSmem residual_smem(int L, int npp, int S, int
   return s;
 }
 
+// One CTA pass over chunk c of problem P: the chunk's items (one per team),
+// its staged channels and preprocessing.  `rezero`: clear the staging area
+// first (the layout changed since the last chunk this CTA ran).
 template <int NPP, int S>
-__global__ void __launch_bounds__(128, 3)
-ocd_residual_kernel(const DetectParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void residual_chunk(const DetectParams& P, long long c,
+                                               unsigned char* smem_raw, bool rezero) {
   const int teams = blockDim.x >> P.logL;
   const ResidualSmem lay = residual_smem(P.L, NPP, S, P.U, P.scmax, teams);
   float2* sH = reinterpret_cast<float2*>(smem_raw);
@@ -76,10 +79,6 @@ ocd_residual_kernel(const DetectParams P) {
   const int T = P.T;
   const int G = (T + S - 1) / S;  // symbol groups per subcarrier
 
-  // Spare slots and antennas >= B stay zero for the whole kernel: staging
-  // below only ever writes the slots of antennas < B.
-  for (int i = tid; i < P.scmax * lay.sc_stride; i += nt) sH[i] = make_float2(0.0f, 0.0f);
-
   // Staging geometry: a warp copies `rows` antenna rows of U entries at a time
   // (coalesced), lane -> (row my_r, user my_u); lanes past rows*U idle.
   const int rows = 32 / U;
@@ -90,8 +89,7 @@ ocd_residual_kernel(const DetectParams P) {
 
   float2* zt = s_z + team * S * kUserSlots;
 
-  const long long nchunks = (P.items + P.chunk - 1) / P.chunk;
-  for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+  {
     const long long i0 = c * P.chunk;
     const long long i1 = min(i0 + (long long)P.chunk, P.items);
     const long long sc0 = i0 / G;
@@ -132,6 +130,12 @@ ocd_residual_kernel(const DetectParams P) {
     }
 
     __syncthreads();  // the previous chunk is no longer being read
+    if (rezero) {
+      // spare slots and antennas >= B stay zero while the layout is kept:
+      // staging only ever writes the slots of antennas < B
+      for (int i = tid; i < P.scmax * lay.sc_stride; i += nt) sH[i] = make_float2(0.0f, 0.0f);
+      __syncthreads();
+    }
     // ---- stage H[sc0 .. sc0+nsc) as user-major columns (8 loads in flight) --
     if (stager) {
       for (int s = 0; s < nsc; ++s) {
@@ -267,6 +271,41 @@ ocd_residual_kernel(const DetectParams P) {
         }
       }
     }
+  }
+}
+
+// Single problem: CTA b takes chunks b, b + gridDim.x, ...
+template <int NPP, int S>
+__global__ void __launch_bounds__(128, 3)
+ocd_residual_kernel(const __grid_constant__ DetectParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long nchunks = (P.items + P.chunk - 1) / P.chunk;
+  for (long long c = blockIdx.x; c < nchunks; c += gridDim.x)
+    residual_chunk<NPP, S>(P, c, smem_raw, c == blockIdx.x);
+}
+
+// Several problems in one persistent launch: each CTA draws tickets (one
+// chunk of one cell each) from a device counter; tickets of cell c are
+// [tick_end[c-1], tick_end[c]).  Cells of one launch share NPP, S and the
+// block size; the staging layout is rebuilt when a CTA moves to a new cell.
+template <int NPP, int S>
+__global__ void __launch_bounds__(128, 3)
+ocd_batched_residual_kernel(const __grid_constant__ BatchTable tab,
+                            unsigned int* __restrict__ tickets) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned int s_ticket;
+  int c = 0, last = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(tickets, 1u);
+    __syncthreads();
+    const unsigned int tk = s_ticket;
+    // every thread has read s_ticket before thread 0 can overwrite it: the
+    // chunk below passes further barriers, and the exit is uniform
+    if (tk >= tab.total) return;
+    while (tk >= tab.cell[c].tick_end) ++c;  // a CTA's tickets increase
+    const long long t0 = c ? tab.cell[c - 1].tick_end : 0;
+    residual_chunk<NPP, S>(tab.cell[c].P, (long long)tk - t0, smem_raw, c != last);
+    last = c;
   }
 }
 

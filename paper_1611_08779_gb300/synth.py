@@ -117,3 +117,32 @@ def make_noiseless(Nsc: int, B: int, U: int, T: int, order: int, seed: int,
     d["Y"] = np.ascontiguousarray(np.matmul(d["S"], np.swapaxes(d["H"], 1, 2)))
     d["N0"] = 0.0
     return d
+
+
+# Cell mix of the batched form: per cell (B, U) from these pairs, a subcarrier
+# count uniform in [nsc_lo, nsc_hi], T from MIXED_T, K uniform in [2, 5], MMSE
+# or BOX, 16- or 64-QAM, SNR uniform in [snr_lo, snr_hi] dB.
+MIXED_BU = ((32, 4), (64, 8), (128, 16), (256, 32))
+MIXED_T = (1, 7, 14)
+
+
+def mixed_cell_specs(ncells: int, seed: int, nsc_lo: int = 300, nsc_hi: int = 3300,
+                     snr_lo: float = 5.0, snr_hi: float = 25.0) -> list[dict]:
+    """Seeded parameters of `ncells` independent cells; every (B, U) pair and
+    every T appear when ncells >= 12 (cells i cycle through the pairs and the
+    symbol counts), the rest is drawn."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(ncells):
+        B, U = MIXED_BU[i % len(MIXED_BU)]
+        T = MIXED_T[(i // len(MIXED_BU)) % len(MIXED_T)]
+        specs.append({
+            "B": B, "U": U, "T": T,
+            "Nsc": int(rng.integers(nsc_lo, nsc_hi + 1)),
+            "K": int(rng.integers(2, 6)),
+            "mode": "box" if rng.integers(0, 2) else "mmse",
+            "order": 64 if rng.integers(0, 2) else 16,
+            "snr_db": float(rng.uniform(snr_lo, snr_hi)),
+            "seed": int(rng.integers(0, 2**31 - 1)),
+        })
+    return specs
