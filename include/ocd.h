@@ -248,6 +248,59 @@ int ocd_graph_create_batched(const ocd_cell_t* cells, int ncells, const ocd_tune
 int ocd_graph_launch(ocd_graph_t* graph, cudaStream_t stream);
 int ocd_graph_destroy(ocd_graph_t* graph);
 
+/* ---------------------------------------------------------------------------
+ * Unfolded (differentiable) form.  Not in the paper: Algorithm 1 with K fixed
+ * sweeps whose regularizer alpha_k and damping omega_k are learnable per
+ * sweep.  Sweep k uses d_{u,k} = 1/(||h_u||^2 + alpha_k), p_{u,k} =
+ * d_{u,k} ||h_u||^2 (both 0 when the denominator is <= 0) and the update
+ *     c = proj(d_{u,k} h_u^H r + p_{u,k} z_u),  dz = omega_k (c - z_u),
+ *     z_u <- z_u + dz,  r <- r - h_u dz
+ * (omega_k = 1 and alpha_k = alpha give Algorithm 1).  Soft output: Eq. 9
+ * with mu~ = p_{u,K} and rho~ = ||h_u||^2 Es / N0[w].  The adjoint treats
+ * the projection's derivative as 1 strictly inside the box and 0 on or
+ * outside its bound, and passes the derivative of Eq. 9's minima to the
+ * minimizing level.  H and Y are complex64 only.
+ * ------------------------------------------------------------------------- */
+
+/* Device bytes of the per-sweep checkpoints (r and z at the start of each
+ * sweep, complex64 [K][Nsc*T][B+U]). */
+size_t ocd_unfolded_checkpoint_size(int Nsc, int B, int U, int T, int K);
+/* Device workspace bytes of ocd_unfolded_backward (per-sample partial
+ * gradients; a multiple of 256). */
+size_t ocd_unfolded_workspace_size(int Nsc, int T, int K);
+
+/*
+ * ocd_unfolded_forward -- the unfolded sweeps and soft output.
+ *   H, Y        device complex64, layouts as ocd_detect.
+ *   N0          device float [Nsc]: noise variance per subcarrier (> 0 where
+ *               LLRs are requested; not checked on the host).
+ *   K           1..OCD_MAX_SWEEPS; omega, alpha: device float [K].
+ *   xhat        device complex64 [Nsc][T][U] (required: the adjoint reads it).
+ *   llr         device float [Nsc][T][U][Q] or NULL.
+ *   ckpt        device buffer of ocd_unfolded_checkpoint_size(...) bytes,
+ *               written here and read by ocd_unfolded_backward.
+ */
+int ocd_unfolded_forward(const void* H, const void* Y, int Nsc, int B, int U, int T,
+                         const float* N0, float Es, int K, int mode, int qam_order,
+                         const float* omega, const float* alpha, void* xhat, float* llr,
+                         void* ckpt, cudaStream_t stream);
+
+/*
+ * ocd_unfolded_backward -- gradients of a loss with respect to omega and
+ * alpha, given its gradients with respect to xhat (dxhat, complex64
+ * [Nsc][T][U], adjoint convention dl/dRe + i dl/dIm) and to the LLRs (dllr,
+ * float [Nsc][T][U][Q]); either may be NULL.  H, N0, omega, alpha, xhat and
+ * ckpt are those of the forward call (unchanged since).  Writes domega and
+ * dalpha (device float [K]; summed over all samples in a fixed order, so the
+ * result is deterministic).  workspace: ocd_unfolded_workspace_size(Nsc, T,
+ * K) device bytes, 4-byte aligned.
+ */
+int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const float* N0,
+                          float Es, int K, int mode, int qam_order, const float* omega,
+                          const float* alpha, const void* xhat, const void* ckpt,
+                          const void* dxhat, const float* dllr, float* domega, float* dalpha,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* ocd_last_error(void);
 

@@ -120,7 +120,7 @@ def unfolded_loss_and_grad(H, Y, N0, Es, omega, alpha, mode, order, bits):
     _, llr = unfolded_forward(H, Y, N0, Es, om, al, mode, order)
     loss = bce_loss(llr, bits)
     loss.backward()
-    return float(loss), om.grad.numpy().copy(), al.grad.numpy().copy()
+    return float(loss.detach()), om.grad.numpy().copy(), al.grad.numpy().copy()
 
 
 __all__ = ["BOX", "MMSE", "unfolded_forward", "maxlog_llr", "bce_loss", "unfolded_loss_and_grad"]

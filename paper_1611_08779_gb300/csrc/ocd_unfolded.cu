@@ -1,0 +1,484 @@
+// Unfolded OCD with a learnable damping omega_k and regularizer alpha_k per
+// sweep (the differentiable form): forward kernel with per-sweep
+// checkpoints, hand-written adjoint kernel, and the deterministic reduction
+// of the parameter gradients.  See include/ocd.h for the C entry points.
+//
+// Forward, per (subcarrier w, symbol t) and sweep k = 1..K (Algorithm 1 with
+// two changes):
+//   d_{u,k} = 1/(||h_u||^2 + alpha_k), p_{u,k} = d_{u,k} ||h_u||^2
+//   c = proj(d_{u,k} h_u^H r + p_{u,k} z_u),  dz = omega_k (c - z_u)
+//   z_u <- z_u + dz,  r <- r - h_u dz                     (Eq. 15 kept)
+// soft output as Eq. 9 with mu~ = p_{u,K}, rho~ = ||h_u||^2 Es / N0[w].
+//
+// Adjoint of one user update (complex adjoints v' = dl/dRe v + i dl/dIm v;
+// primes denote adjoints of the values after the update):
+//   g     = z_u' - h_u^H r'                  (adjoint of dz)
+//   omega_k'  += Re<c - z_u, g>
+//   w'    = mask(omega_k g)                  (mask: 1 strictly inside the box, else 0)
+//   z_u'  <- z_u' - omega_k g + p w'
+//   r'    <- r' + d h_u w'
+//   alpha_k'  += -d^2 Re<h_u^H r, w'> - p d Re<z_u, w'>
+// The sweep's inputs (r and z at its start) are checkpointed by the forward
+// kernel; the adjoint replays the sweep from its checkpoint (bit-identical
+// arithmetic) to recover each update's z_u and h_u^H r, then runs the users
+// in reverse.
+//
+// Layout: one warp per (subcarrier, symbol) sample; lane l holds the
+// residual (and its adjoint) of antennas l + 32 j, j < NA; lane u holds z_u,
+// ||h_u||^2 and the adjoint of z_u.
+#include <cuda_runtime.h>
+
+#include "ocd_common.cuh"
+#include "ocd_unfolded.h"
+
+namespace ocd {
+
+namespace {
+
+__device__ __forceinline__ float2 warp_sum2(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(kFullMask, v.x, o);
+    v.y += __shfl_xor_sync(kFullMask, v.y, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(kFullMask, v.x, src), __shfl_sync(kFullMask, v.y, src));
+}
+
+// d and p of sweep k for a user with squared norm n (0, 0 for a zero or
+// negative denominator).
+__device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) {
+  const float den = n + alpha;
+  d = den > 0.0f ? 1.0f / den : 0.0f;
+  p = d * n;
+}
+
+template <int NA>
+struct Warp {
+  const UnfoldParams& P;
+  const float2* Hw;  // channel of this sample's subcarrier, [B][U]
+  int lane;
+
+  __device__ __forceinline__ void load_h(int u, float2 (&h)[NA]) const {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int b = lane + 32 * j;
+      h[j] = b < P.B ? __ldg(Hw + (long long)b * P.U + u) : make_float2(0.0f, 0.0f);
+    }
+  }
+
+  // lane u (< U) receives ||h_u||^2
+  __device__ __forceinline__ float norms() const {
+    float mine = 0.0f;
+    for (int u = 0; u < P.U; ++u) {
+      float2 h[NA];
+      load_h(u, h);
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) acc = fmaf(h[j].x, h[j].x, fmaf(h[j].y, h[j].y, acc));
+      acc = warp_sum(acc);
+      if (lane == u) mine = acc;
+    }
+    return mine;
+  }
+
+  // One forward sweep.  z: lane u holds z_u.  When `keep` is set, lane u
+  // records z_u before its update (zb) and h_u^H r at that time (qs).
+  template <bool KEEP>
+  __device__ __forceinline__ void sweep(float2 (&r)[NA], float2& z, float nrm, float om, float al,
+                                        float2& zb, float2& qs) const {
+    for (int u = 0; u < P.U; ++u) {
+      float2 h[NA];
+      load_h(u, h);
+      float2 q = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        q.x = fmaf(h[j].x, r[j].x, fmaf(h[j].y, r[j].y, q.x));
+        q.y = fmaf(h[j].x, r[j].y, fmaf(-h[j].y, r[j].x, q.y));
+      }
+      q = warp_sum2(q);
+      float d, p;
+      gains(__shfl_sync(kFullMask, nrm, u), al, d, p);
+      const float2 zu = shfl2(z, u);
+      float wr = fmaf(d, q.x, p * zu.x);
+      float wi = fmaf(d, q.y, p * zu.y);
+      project(wr, wi, P.D);
+      const float2 dz = make_float2(om * (wr - zu.x), om * (wi - zu.y));
+      if (lane == u) {
+        if (KEEP) {
+          zb = zu;
+          qs = q;
+        }
+        z = make_float2(zu.x + dz.x, zu.y + dz.y);
+      }
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        r[j].x = fmaf(-h[j].x, dz.x, fmaf(h[j].y, dz.y, r[j].x));
+        r[j].y = fmaf(-h[j].x, dz.y, fmaf(-h[j].y, dz.x, r[j].y));
+      }
+    }
+  }
+};
+
+template <int NA>
+__global__ void __launch_bounds__(128)
+ocd_unfolded_forward_kernel(const __grid_constant__ UnfoldParams P) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  const int stride = P.B + P.U;
+  for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.samples;
+       s += nw) {
+    const long long w = s / P.T;
+    Warp<NA> W{P, P.H + w * P.B * P.U, lane};
+    const float nrm = W.norms();
+    float2 r[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int b = lane + 32 * j;
+      r[j] = b < P.B ? __ldg(P.Y + s * P.B + b) : make_float2(0.0f, 0.0f);
+    }
+    float2 z = make_float2(0.0f, 0.0f), zb = z, qs = z;
+    for (int k = 0; k < P.K; ++k) {
+      float2* ck = P.ckpt + ((long long)k * P.samples + s) * stride;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int b = lane + 32 * j;
+        if (b < P.B) ck[b] = r[j];
+      }
+      if (lane < P.U) ck[P.B + lane] = z;
+      W.template sweep<false>(r, z, nrm, __ldg(P.omega + k), __ldg(P.alpha + k), zb, qs);
+    }
+    if (lane < P.U) {
+      const long long o = s * P.U + lane;
+      P.xhat[o] = z;
+      if (P.llr) {
+        float d, p;
+        gains(nrm, __ldg(P.alpha + P.K - 1), d, p);
+        DetectParams D = P.D;
+        D.rho_scale = P.es / __ldg(P.N0 + w);
+        user_llr(z, nrm, p, D, P.llr + o * P.D.Q);
+      }
+    }
+  }
+}
+
+// d/dx of sum_b g_b L_b(x) for the bits of one real dimension (Eq. 9 per
+// dimension): L_b = rho (min_{bit b = 0} (x - v)^2 - min_{bit b = 1} (x - v)^2)
+// is linear in x between changes of the minimizing levels v0*, v1*, with
+// slope 2 rho (v1* - v0*).
+__device__ __forceinline__ float dimension_llr_slope(float x, float rho, const DetectParams& D,
+                                                     const float* g) {
+  const int nb = D.nb, M = D.M;
+  float b0[4], b1[4], v0[4], v1[4];
+  for (int j = 0; j < nb; ++j) { b0[j] = FLT_MAX; b1[j] = FLT_MAX; v0[j] = 0.0f; v1[j] = 0.0f; }
+  for (int i = 0; i < M; ++i) {
+    const float v = (float)(2 * i + 1 - M) * D.lvl_step;
+    const float e = x - v;
+    const float dd = e * e;
+    const int gw = i ^ (i >> 1);
+    for (int j = 0; j < nb; ++j) {
+      if ((gw >> (nb - 1 - j)) & 1) {
+        if (dd < b1[j]) { b1[j] = dd; v1[j] = v; }
+      } else {
+        if (dd < b0[j]) { b0[j] = dd; v0[j] = v; }
+      }
+    }
+  }
+  float s = 0.0f;
+  for (int j = 0; j < nb; ++j) s = fmaf(g[j], 2.0f * rho * (v1[j] - v0[j]), s);
+  return s;
+}
+
+template <int NA>
+__global__ void __launch_bounds__(128)
+ocd_unfolded_backward_kernel(const __grid_constant__ UnfoldParams P) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  const int stride = P.B + P.U;
+  const int K = P.K;
+  for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.samples;
+       s += nw) {
+    const long long w = s / P.T;
+    Warp<NA> W{P, P.H + w * P.B * P.U, lane};
+    const float nrm = W.norms();
+    // ---- adjoint of the soft output and of xhat (lane u)
+    float2 zbar = make_float2(0.0f, 0.0f);
+    float al_mu = 0.0f;  // alpha_K' through mu~ = p_{u,K}
+    if (lane < P.U) {
+      const long long o = s * P.U + lane;
+      if (P.dxhat) zbar = __ldg(P.dxhat + o);
+      if (P.dllr) {
+        float d, p;
+        gains(nrm, __ldg(P.alpha + K - 1), d, p);
+        if (p > 0.0f) {
+          const float2 z = __ldg(P.xhat + o);
+          const float rho = nrm * P.es / __ldg(P.N0 + w);
+          const float inv = 1.0f / (p * P.D.sqrt_es);
+          const float* g = P.dllr + o * P.D.Q;
+          const float xr = z.x * inv;
+          const float sr = dimension_llr_slope(xr, rho, P.D, g);
+          zbar.x += sr * inv;
+          float mubar = -sr * xr / p;
+          if (!P.D.bpsk) {
+            const float xi = z.y * inv;
+            const float si = dimension_llr_slope(xi, rho, P.D, g + P.D.nb);
+            zbar.y += si * inv;
+            mubar -= si * xi / p;
+          }
+          al_mu = mubar * (-p * d);
+        }
+      }
+    }
+    al_mu = warp_sum(al_mu);
+    float2 rbar[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) rbar[j] = make_float2(0.0f, 0.0f);
+    float* part = P.partial + s * 2 * K;
+    for (int k = K - 1; k >= 0; --k) {
+      const float om = __ldg(P.omega + k);
+      const float al = __ldg(P.alpha + k);
+      // replay sweep k from its checkpoint
+      const float2* ck = P.ckpt + ((long long)k * P.samples + s) * stride;
+      float2 r[NA];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int b = lane + 32 * j;
+        r[j] = b < P.B ? ck[b] : make_float2(0.0f, 0.0f);
+      }
+      float2 z = lane < P.U ? ck[P.B + lane] : make_float2(0.0f, 0.0f);
+      float2 zb = make_float2(0.0f, 0.0f), qs = make_float2(0.0f, 0.0f);
+      W.template sweep<true>(r, z, nrm, om, al, zb, qs);
+      // reverse over the users
+      float om_bar = 0.0f, al_bar = 0.0f;
+      for (int u = P.U - 1; u >= 0; --u) {
+        float2 h[NA];
+        W.load_h(u, h);
+        const float2 zu = shfl2(zb, u);
+        const float2 q = shfl2(qs, u);
+        float d, p;
+        gains(__shfl_sync(kFullMask, nrm, u), al, d, p);
+        const float wr0 = fmaf(d, q.x, p * zu.x);
+        const float wi0 = fmaf(d, q.y, p * zu.y);
+        float cr = wr0, ci = wi0;
+        project(cr, ci, P.D);
+        float mr = 1.0f, mi = 1.0f;
+        if (P.D.box) {
+          mr = fabsf(wr0) < P.D.box_a ? 1.0f : 0.0f;
+          mi = (!P.D.bpsk && fabsf(wi0) < P.D.box_a) ? 1.0f : 0.0f;
+        }
+        // h_u^H r'
+        float2 hr = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          hr.x = fmaf(h[j].x, rbar[j].x, fmaf(h[j].y, rbar[j].y, hr.x));
+          hr.y = fmaf(h[j].x, rbar[j].y, fmaf(-h[j].y, rbar[j].x, hr.y));
+        }
+        hr = warp_sum2(hr);
+        const float2 zbu = shfl2(zbar, u);
+        const float gr = zbu.x - hr.x, gi = zbu.y - hr.y;
+        om_bar = fmaf(cr - zu.x, gr, fmaf(ci - zu.y, gi, om_bar));
+        const float wbr = mr * om * gr, wbi = mi * om * gi;
+        if (lane == u) zbar = make_float2(zbu.x - om * gr + p * wbr, zbu.y - om * gi + p * wbi);
+        const float dwr = d * wbr, dwi = d * wbi;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          rbar[j].x = fmaf(h[j].x, dwr, fmaf(-h[j].y, dwi, rbar[j].x));
+          rbar[j].y = fmaf(h[j].x, dwi, fmaf(h[j].y, dwr, rbar[j].y));
+        }
+        al_bar -= d * d * fmaf(q.x, wbr, q.y * wbi) + p * d * fmaf(zu.x, wbr, zu.y * wbi);
+      }
+      if (k == K - 1) al_bar += al_mu;
+      if (lane == 0) {
+        part[2 * k] = om_bar;
+        part[2 * k + 1] = al_bar;
+      }
+    }
+  }
+}
+
+// out[j] = sum over samples of partial[s][j], j < 2K, in a fixed order.
+__global__ void __launch_bounds__(256)
+ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples, int K,
+                           float* __restrict__ domega, float* __restrict__ dalpha) {
+  __shared__ float red[256];
+  const int j = blockIdx.x;  // 0 .. 2K-1
+  float acc = 0.0f;
+  for (long long s = threadIdx.x; s < samples; s += blockDim.x) acc += partial[s * 2 * K + j];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (j & 1) dalpha[j >> 1] = red[0];
+    else domega[j >> 1] = red[0];
+  }
+}
+
+template <int NA>
+cudaError_t launch_pair(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
+  if (backward) ocd_unfolded_backward_kernel<NA><<<grid, 128, 0, stream>>>(P);
+  else ocd_unfolded_forward_kernel<NA><<<grid, 128, 0, stream>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_unfolded(const UnfoldParams& P, bool backward, int sms, cudaStream_t stream) {
+  if (P.samples == 0) return cudaSuccess;
+  long long grid = (P.samples + 3) / 4;
+  const long long cap = (long long)sms * 16;
+  if (grid > cap) grid = cap;
+  const int na = (P.B + 31) / 32;
+  cudaError_t e;
+  if (na <= 1) e = launch_pair<1>(P, backward, (unsigned)grid, stream);
+  else if (na <= 2) e = launch_pair<2>(P, backward, (unsigned)grid, stream);
+  else if (na <= 4) e = launch_pair<4>(P, backward, (unsigned)grid, stream);
+  else if (na <= 8) e = launch_pair<8>(P, backward, (unsigned)grid, stream);
+  else e = launch_pair<16>(P, backward, (unsigned)grid, stream);
+  if (e != cudaSuccess || !backward) return e;
+  ocd_unfolded_reduce_kernel<<<2 * P.K, 256, 0, stream>>>(P.partial, P.samples, P.K, P.domega,
+                                                          P.dalpha);
+  return cudaGetLastError();
+}
+
+}  // namespace ocd
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+#include <math.h>
+#include <string.h>
+
+#include "ocd.h"
+#include "ocd_host.h"
+
+using namespace ocdh;
+
+namespace {
+
+int unfolded_common(const void* H, int Nsc, int B, int U, int T, const float* N0, float Es,
+                    int K, int mode, int qam_order, const float* omega, const float* alpha,
+                    const void* xhat, const void* ckpt, ocd::UnfoldParams& P) {
+  Alphabet al;
+  if (Nsc < 0 || T < 0) return fail(OCD_ERR_ARG, "Nsc=%d and T=%d must be >= 0", Nsc, T);
+  if (B < 1 || B > OCD_MAX_ANTENNAS) return fail(OCD_ERR_ARG, "B=%d outside 1..%d", B, OCD_MAX_ANTENNAS);
+  if (U < 1 || U > OCD_MAX_USERS) return fail(OCD_ERR_ARG, "U=%d outside 1..%d", U, OCD_MAX_USERS);
+  if (K < 1 || K > OCD_MAX_SWEEPS) return fail(OCD_ERR_ARG, "K=%d outside 1..%d", K, OCD_MAX_SWEEPS);
+  if (mode != OCD_MMSE && mode != OCD_BOX) return fail(OCD_ERR_ARG, "unknown mode %d", mode);
+  if (!alphabet_of(qam_order, al)) return fail(OCD_ERR_ARG, "unsupported qam_order %d", qam_order);
+  if (!(Es > 0.0f) || !isfinite(Es)) return fail(OCD_ERR_ARG, "Es must be finite and > 0");
+  const long long samples = (long long)Nsc * T;
+  if (samples > 0 && (!H || !N0 || !omega || !alpha || !xhat || !ckpt))
+    return fail(OCD_ERR_ARG, "H, N0, omega, alpha, xhat and ckpt must not be NULL");
+  if ((((uintptr_t)H | (uintptr_t)xhat | (uintptr_t)ckpt) & 7u) ||
+      (((uintptr_t)N0 | (uintptr_t)omega | (uintptr_t)alpha) & 3u))
+    return fail(OCD_ERR_ARG, "arrays must be aligned to their element size");
+  memset(&P, 0, sizeof(P));
+  build_params(H, nullptr, OCD_STORE_C64, Nsc, B, U, T, 1.0f, Es, K, mode, al, const_cast<void*>(xhat),
+               nullptr, P.D);
+  P.H = static_cast<const float2*>(H);
+  P.N0 = N0;
+  P.omega = omega;
+  P.alpha = alpha;
+  P.xhat = static_cast<float2*>(const_cast<void*>(xhat));
+  P.ckpt = static_cast<float2*>(const_cast<void*>(ckpt));
+  P.samples = samples;
+  P.Nsc = Nsc; P.B = B; P.U = U; P.T = T; P.K = K;
+  P.es = Es;
+  return OCD_OK;
+}
+
+int sms_of_current(int& sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  DeviceInfo di;
+  const int st = device_info(dev, di);
+  if (st != OCD_OK) return st;
+  sms = di.sms;
+  return OCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ocd_unfolded_checkpoint_size(int Nsc, int B, int U, int T, int K) {
+  if (Nsc <= 0 || T <= 0 || B <= 0 || U <= 0 || K <= 0) return 0;
+  return (size_t)K * Nsc * T * (B + U) * sizeof(float2);
+}
+
+size_t ocd_unfolded_workspace_size(int Nsc, int T, int K) {
+  if (Nsc <= 0 || T <= 0 || K <= 0) return 0;
+  const size_t b = (size_t)Nsc * T * 2 * K * sizeof(float);
+  return (b + 255) / 256 * 256;
+}
+
+int ocd_unfolded_forward(const void* H, const void* Y, int Nsc, int B, int U, int T,
+                         const float* N0, float Es, int K, int mode, int qam_order,
+                         const float* omega, const float* alpha, void* xhat, float* llr,
+                         void* ckpt, cudaStream_t stream) {
+  ocd::UnfoldParams P;
+  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt, P);
+  if (st != OCD_OK) return st;
+  if (P.samples > 0 && !Y) return fail(OCD_ERR_ARG, "Y must not be NULL");
+  if (((uintptr_t)Y & 7u) || ((uintptr_t)llr & 3u))
+    return fail(OCD_ERR_ARG, "arrays must be aligned to their element size");
+  if (P.samples == 0) return OCD_OK;
+  P.Y = static_cast<const float2*>(Y);
+  P.llr = llr;
+  int sms = 0;
+  st = sms_of_current(sms);
+  if (st != OCD_OK) return st;
+  const cudaError_t e = ocd::launch_unfolded(P, false, sms, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "unfolded forward launch");
+  return OCD_OK;
+}
+
+int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const float* N0,
+                          float Es, int K, int mode, int qam_order, const float* omega,
+                          const float* alpha, const void* xhat, const void* ckpt,
+                          const void* dxhat, const float* dllr, float* domega, float* dalpha,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  ocd::UnfoldParams P;
+  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt, P);
+  if (st != OCD_OK) return st;
+  if (!domega || !dalpha) return fail(OCD_ERR_ARG, "domega and dalpha must not be NULL");
+  if (((uintptr_t)dxhat & 7u) || (((uintptr_t)dllr | (uintptr_t)domega | (uintptr_t)dalpha |
+                                   (uintptr_t)workspace) & 3u))
+    return fail(OCD_ERR_ARG, "arrays must be aligned to their element size");
+  if (P.samples > 0 && (!workspace || workspace_bytes < ocd_unfolded_workspace_size(Nsc, T, K)))
+    return fail(OCD_ERR_ARG, "workspace of %zu bytes is smaller than the %zu needed",
+                workspace_bytes, ocd_unfolded_workspace_size(Nsc, T, K));
+  cudaError_t e;
+  if (P.samples == 0) {
+    e = cudaMemsetAsync(domega, 0, K * sizeof(float), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dalpha, 0, K * sizeof(float), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    return OCD_OK;
+  }
+  P.dxhat = static_cast<const float2*>(dxhat);
+  P.dllr = dllr;
+  P.partial = static_cast<float*>(workspace);
+  P.domega = domega;
+  P.dalpha = dalpha;
+  int sms = 0;
+  st = sms_of_current(sms);
+  if (st != OCD_OK) return st;
+  e = ocd::launch_unfolded(P, true, sms, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "unfolded backward launch");
+  return OCD_OK;
+}
+
+}  // extern "C"

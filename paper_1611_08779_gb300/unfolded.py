@@ -1,0 +1,87 @@
+"""Python binding of the unfolded (differentiable) OCD: a
+torch.autograd.Function whose forward and backward are the library's
+ocd_unfolded_forward / ocd_unfolded_backward (argument marshalling only).
+
+The learnable parameters are the per-sweep damping omega [K] and regularizer
+alpha [K] (float32 CUDA tensors); H, Y and the per-subcarrier noise variance
+N0 [Nsc] are data.  Gradients flow to omega and alpha only.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native
+from .api import _check_c64, _mode, _stream_handle, bits_per_symbol
+
+
+def _f32(name, t, n, dev):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.device != dev \
+            or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be a contiguous float32 tensor of {n} elements on {dev}")
+
+
+class UnfoldedOCD(torch.autograd.Function):
+    """(omega, alpha, H, Y, N0, Es, mode, qam_order) -> (xhat, llr)."""
+
+    @staticmethod
+    def forward(ctx, omega, alpha, H, Y, N0, Es=1.0, mode="box", qam_order=16):
+        lib = _native.load()
+        _check_c64("H", H)
+        _check_c64("Y", Y, H.device)
+        dev = H.device
+        if dev.type != "cuda":
+            raise ValueError("H must be a CUDA tensor (the detector has no CPU path)")
+        Nsc, B, U = H.shape
+        T = Y.shape[1]
+        if tuple(Y.shape) != (Nsc, T, B):
+            raise ValueError(f"Y shape {tuple(Y.shape)} does not match H {tuple(H.shape)}")
+        K = omega.numel()
+        _f32("omega", omega, K, dev)
+        _f32("alpha", alpha, K, dev)
+        _f32("N0", N0, Nsc, dev)
+        Q = bits_per_symbol(qam_order)
+        xhat = torch.empty((Nsc, T, U), dtype=torch.complex64, device=dev)
+        llr = torch.empty((Nsc, T, U, Q), dtype=torch.float32, device=dev)
+        nck = lib.ocd_unfolded_checkpoint_size(Nsc, B, U, T, K)
+        ckpt = torch.empty(max(int(nck), 8), dtype=torch.uint8, device=dev)
+        with torch.cuda.device(dev):
+            st = lib.ocd_unfolded_forward(H.data_ptr(), Y.data_ptr(), Nsc, B, U, T, N0.data_ptr(),
+                                          float(Es), K, _mode(mode), int(qam_order),
+                                          omega.data_ptr(), alpha.data_ptr(), xhat.data_ptr(),
+                                          llr.data_ptr(), ckpt.data_ptr(), _stream_handle(None))
+        _native.check(st)
+        ctx.save_for_backward(omega, alpha, H, N0, xhat, ckpt)
+        ctx.args = (float(Es), _mode(mode), int(qam_order))
+        return xhat, llr
+
+    @staticmethod
+    def backward(ctx, gx, gl):
+        lib = _native.load()
+        omega, alpha, H, N0, xhat, ckpt = ctx.saved_tensors
+        Es, mode, order = ctx.args
+        Nsc, B, U = H.shape
+        T = xhat.shape[1]
+        K = omega.numel()
+        dev = H.device
+        gx = gx.contiguous() if gx is not None else None
+        gl = gl.contiguous().float() if gl is not None else None
+        domega = torch.empty(K, dtype=torch.float32, device=dev)
+        dalpha = torch.empty(K, dtype=torch.float32, device=dev)
+        nws = lib.ocd_unfolded_workspace_size(Nsc, T, K)
+        ws = torch.empty(max(int(nws), 256), dtype=torch.uint8, device=dev)
+        with torch.cuda.device(dev):
+            st = lib.ocd_unfolded_backward(H.data_ptr(), Nsc, B, U, T, N0.data_ptr(), Es, K, mode,
+                                           order, omega.data_ptr(), alpha.data_ptr(),
+                                           xhat.data_ptr(), ckpt.data_ptr(),
+                                           gx.data_ptr() if gx is not None else None,
+                                           gl.data_ptr() if gl is not None else None,
+                                           domega.data_ptr(), dalpha.data_ptr(), ws.data_ptr(),
+                                           ws.numel(), _stream_handle(None))
+        _native.check(st)
+        return domega, dalpha, None, None, None, None, None, None
+
+
+def unfolded_ocd(omega, alpha, H, Y, N0, Es=1.0, mode="box", qam_order=16):
+    """Differentiable unfolded OCD: returns (xhat, llr); gradients reach
+    omega and alpha through the library's adjoint kernel."""
+    return UnfoldedOCD.apply(omega, alpha, H, Y, N0, Es, mode, qam_order)

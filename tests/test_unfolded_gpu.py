@@ -1,0 +1,208 @@
+"""Unfolded (differentiable) OCD on the GPU: forward values against the FP64
+reference of oracle/unfolded.py, gradients of the BCE loss with respect to
+the per-sweep damping and regularizer against FP64 autograd and against
+finite differences of the GPU forward, and the edge cases of the adjoint."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc  # noqa: E402
+import paper_1611_08779_gb300 as ocd  # noqa: E402
+from paper_1611_08779_gb300 import synth  # noqa: E402
+
+from .parity import hard_bit_mismatches, llr_excess, xhat_error  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+MODE = {"box": orc.BOX, "mmse": orc.MMSE}
+
+
+def problem(Nsc, B, U, T, order, seed, snr_lo=5.0, snr_hi=25.0):
+    """Per-subcarrier SNR uniform in [snr_lo, snr_hi] dB (N0 per subcarrier)."""
+    rng = np.random.default_rng(seed)
+    snr = rng.uniform(snr_lo, snr_hi, size=Nsc)
+    N0 = 10.0 ** (-snr / 10.0)
+    d = synth.make_uplink(Nsc, B, U, T, order, 100.0, seed, dtype=np.complex128)  # noiseless
+    noise = (rng.standard_normal(d["Y"].shape) + 1j * rng.standard_normal(d["Y"].shape))
+    Y = d["Y"] + noise * np.sqrt(N0 / 2.0)[:, None, None]
+    return d["H"].astype(np.complex64), Y.astype(np.complex64), N0.astype(np.float32), d["bits"]
+
+
+def to_dev(H, Y, N0):
+    return torch.from_numpy(H).cuda(), torch.from_numpy(Y).cuda(), torch.from_numpy(N0).cuda()
+
+
+def params(K, seed):
+    rng = np.random.default_rng(seed)
+    om = rng.uniform(0.6, 1.3, K).astype(np.float32)
+    al = rng.uniform(0.0, 0.3, K).astype(np.float32)
+    return om, al
+
+
+def reference(H, Y, N0, om, al, mode, order, bits=None):
+    """FP64 values (and loss gradients when bits are given) on the stored float32 inputs."""
+    H64, Y64 = H.astype(np.complex128), Y.astype(np.complex128)
+    N064 = N0.astype(np.float64)
+    if bits is None:
+        with torch.no_grad():
+            z, llr = orc.unfolded_forward(H64, Y64, N064, 1.0, torch.as_tensor(om, dtype=torch.float64),
+                                          torch.as_tensor(al, dtype=torch.float64), MODE[mode], order)
+        return z.numpy(), llr.numpy()
+    return orc.unfolded_loss_and_grad(H64, Y64, N064, 1.0, om.astype(np.float64),
+                                      al.astype(np.float64), MODE[mode], order, bits)
+
+
+def gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t):
+    o = torch.tensor(om, device="cuda", requires_grad=True)
+    a = torch.tensor(al, device="cuda", requires_grad=True)
+    x, llr = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, mode, order)
+    loss = torch.nn.functional.binary_cross_entropy_with_logits(llr, bits_t)
+    loss.backward()
+    return float(loss), o.grad.cpu().numpy(), a.grad.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["box", "mmse"])
+@pytest.mark.parametrize("B,U,T,K,order", [(128, 16, 2, 5, 16), (32, 8, 3, 3, 64), (33, 5, 4, 2, 4),
+                                           (64, 32, 1, 4, 16), (300, 7, 2, 3, 2), (512, 3, 1, 2, 256)])
+def test_forward_matches_the_fp64_reference(mode, B, U, T, K, order):
+    H, Y, N0, _ = problem(12, B, U, T, order, seed=B + U + T + K)
+    om, al = params(K, seed=K)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    x, llr = ocd.unfolded_ocd(torch.tensor(om, device="cuda"), torch.tensor(al, device="cuda"),
+                              Hd, Yd, N0d, 1.0, mode, order)
+    torch.cuda.synchronize()
+    z_ref, l_ref = reference(H, Y, N0, om, al, mode, order)
+    assert xhat_error(x.cpu().numpy(), z_ref) <= 1e-4
+    assert llr_excess(llr.cpu().numpy(), l_ref) <= 1.0
+    n = np.sum(np.abs(H.astype(np.complex128)) ** 2, axis=1)
+    p = n / (n + al[-1])
+    assert hard_bit_mismatches(llr.cpu().numpy(), l_ref, z_ref, p, order) == 0
+
+
+@pytest.mark.parametrize("mode", ["box", "mmse"])
+@pytest.mark.parametrize("B,U,T,K,order", [(128, 16, 2, 5, 16), (48, 8, 4, 3, 64), (20, 3, 3, 2, 2)])
+def test_gradients_match_fp64_autograd(mode, B, U, T, K, order):
+    H, Y, N0, bits = problem(32, B, U, T, order, seed=7 * B + U)
+    om, al = params(K, seed=U + K)
+    loss_ref, gom_ref, gal_ref = reference(H, Y, N0, om, al, mode, order, bits)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    loss, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t)
+    assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
+    g = np.concatenate([gom, gal])
+    g_ref = np.concatenate([gom_ref, gal_ref])
+    assert np.linalg.norm(g - g_ref) <= 2e-3 * np.linalg.norm(g_ref) + 1e-6, (g, g_ref)
+
+
+def test_gradient_matches_finite_differences_of_the_gpu_forward():
+    H, Y, N0, bits = problem(64, 64, 8, 2, 16, seed=31)
+    om, al = params(4, seed=3)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    _, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+
+    def f(o, a):
+        with torch.no_grad():
+            _, llr = ocd.unfolded_ocd(torch.tensor(o, device="cuda"), torch.tensor(a, device="cuda"),
+                                      Hd, Yd, N0d, 1.0, "box", 16)
+            return float(torch.nn.functional.binary_cross_entropy_with_logits(llr.double(), bits_t.double()))
+
+    eps = 2e-3
+    for k in range(4):
+        e = np.zeros(4, dtype=np.float32)
+        e[k] = eps
+        fd_o = (f(om + e, al) - f(om - e, al)) / (2 * eps)
+        fd_a = (f(om, al + e) - f(om, al - e)) / (2 * eps)
+        assert abs(fd_o - gom[k]) <= 3e-2 * max(abs(fd_o), 1e-2), (k, fd_o, gom[k])
+        assert abs(fd_a - gal[k]) <= 3e-2 * max(abs(fd_a), 1e-2), (k, fd_a, gal[k])
+
+
+def test_gradient_through_xhat_only():
+    H, Y, N0, _ = problem(16, 32, 4, 3, 16, seed=41)
+    om, al = params(3, seed=4)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    rng = np.random.default_rng(5)
+    c = (rng.standard_normal((16, 3, 4)) + 1j * rng.standard_normal((16, 3, 4)))
+    o = torch.tensor(om, device="cuda", requires_grad=True)
+    a = torch.tensor(al, device="cuda", requires_grad=True)
+    x, _ = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, "box", 16)
+    (x * torch.from_numpy(c.astype(np.complex64)).cuda()).real.sum().backward()
+    om64 = torch.tensor(om, dtype=torch.float64, requires_grad=True)
+    al64 = torch.tensor(al, dtype=torch.float64, requires_grad=True)
+    z, _ = orc.unfolded_forward(H.astype(np.complex128), Y.astype(np.complex128), N0.astype(np.float64),
+                                1.0, om64, al64, orc.BOX, 16)
+    (z * torch.as_tensor(c)).real.sum().backward()
+    g = np.concatenate([o.grad.cpu().numpy(), a.grad.cpu().numpy()])
+    g_ref = np.concatenate([om64.grad.numpy(), al64.grad.numpy()])
+    assert np.linalg.norm(g - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
+
+
+def test_backward_is_deterministic():
+    H, Y, N0, bits = problem(256, 64, 8, 2, 16, seed=51)
+    om, al = params(3, seed=6)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    r1 = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    r2 = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+
+
+def test_undamped_forward_is_algorithm_1():
+    """omega = 1, alpha = 0 in BOX mode is plain OCD-BOX; with one N0 for all
+    subcarriers it matches the FP64 Algorithm 1 oracle."""
+    d = synth.make_uplink(10, 64, 8, 3, 16, 12.0, 61)
+    Hd = torch.from_numpy(d["H"]).cuda()
+    Yd = torch.from_numpy(d["Y"]).cuda()
+    N0d = torch.full((10,), d["N0"], dtype=torch.float32, device="cuda")
+    x, llr = ocd.unfolded_ocd(torch.ones(3, device="cuda"), torch.zeros(3, device="cuda"),
+                              Hd, Yd, N0d, 1.0, "box", 16)
+    torch.cuda.synchronize()
+    z_ref, l_ref = orc.ocd_detect(d["H"], d["Y"], d["N0"], 1.0, 3, orc.BOX, 16)
+    assert xhat_error(x.cpu().numpy(), z_ref) <= 1e-4
+    assert llr_excess(llr.cpu().numpy(), l_ref) <= 1.0
+
+
+def test_zero_column_and_empty_batch():
+    H, Y, N0, bits = problem(6, 16, 4, 2, 16, seed=71)
+    H[:, :, 2] = 0
+    om, al = params(2, seed=7)
+    al[:] = 0.0  # BOX-like: zero column -> d = p = 0
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    o = torch.tensor(om, device="cuda", requires_grad=True)
+    a = torch.tensor(al, device="cuda", requires_grad=True)
+    x, llr = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, "box", 16)
+    assert torch.all(x[:, :, 2] == 0) and torch.all(llr[:, :, 2] == 0)
+    torch.nn.functional.binary_cross_entropy_with_logits(llr, bits_t).backward()
+    assert torch.all(torch.isfinite(o.grad)) and torch.all(torch.isfinite(a.grad))
+    # no samples: zero gradients
+    He = torch.empty((0, 16, 4), dtype=torch.complex64, device="cuda")
+    Ye = torch.empty((0, 2, 16), dtype=torch.complex64, device="cuda")
+    o2 = torch.tensor(om, device="cuda", requires_grad=True)
+    a2 = torch.tensor(al, device="cuda", requires_grad=True)
+    x, llr = ocd.unfolded_ocd(o2, a2, He, Ye, torch.empty(0, device="cuda"), 1.0, "box", 16)
+    (llr.sum() + x.real.sum()).backward()
+    assert torch.all(o2.grad == 0) and torch.all(a2.grad == 0)
+
+
+def test_a_few_training_steps_reduce_the_loss():
+    """128x16, K = 5, 16-QAM, SNR 5-25 dB: plain gradient steps on omega and
+    alpha from a deliberately poor start lower the BCE loss."""
+    H, Y, N0, bits = problem(256, 128, 16, 1, 16, seed=81)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    o = torch.full((5,), 0.4, device="cuda", requires_grad=True)
+    a = torch.full((5,), 0.5, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([o, a], lr=0.05)
+    losses = []
+    for _ in range(30):
+        opt.zero_grad()
+        _, llr = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, "box", 16)
+        loss = torch.nn.functional.binary_cross_entropy_with_logits(llr, bits_t)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    assert losses[-1] < 0.8 * losses[0], losses
+    assert all(math.isfinite(v) for v in losses)
