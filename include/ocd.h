@@ -224,6 +224,24 @@ int ocd_detect_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tu
                        void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * ocd_detect_batched_static -- ocd_detect_batched without a caller
+ * workspace and without any allocation: the ticket counters live in a
+ * library-owned device array of OCD_STATIC_MAX_CELLS entries (1 KiB per
+ * device), so ncells is limited to OCD_STATIC_MAX_CELLS (OCD_ERR_UNSUPPORTED
+ * beyond, nothing enqueued).  The paper has no counterpart; this is a
+ * serving convenience.  The counters are zeroed on `stream` at the start of
+ * every call.  Races: all calls on one device share the counters, so calls
+ * must not overlap in time -- issue them on one stream or order them with
+ * events (concurrent calls on unordered streams give wrong results).  The
+ * first call on a device looks up the array's address and sets up the
+ * device's kernel attributes; make that call outside stream capture, after
+ * which the call is capturable like ocd_detect_batched.
+ */
+#define OCD_STATIC_MAX_CELLS 256
+int ocd_detect_batched_static(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+                              cudaStream_t stream);
+
+/*
  * ocd_autotune_batched -- for every distinct (B, U, T, storage) among the
  * cells, times the candidate tiles (each arrangement the shape supports;
  * symbols and lanes per item for the residual form, subcarriers per ticket

@@ -27,6 +27,7 @@ OCD_MAX_USERS = 32
 OCD_MAX_ANTENNAS = 512
 OCD_MAX_SWEEPS = 256
 OCD_MAX_CELLS = 1024
+OCD_STATIC_MAX_CELLS = 256
 OCD_TUNE_MAX_ENTRIES = 64
 
 _STATUS = {OCD_ERR_ARG: "OCD_ERR_ARG", OCD_ERR_UNSUPPORTED: "OCD_ERR_UNSUPPORTED",
@@ -69,6 +70,7 @@ SIGNATURES = {
                              _vp, _vp, _vp, _vp, _i, _vp]),
     "ocd_batched_workspace_size": (_sz, [_i]),
     "ocd_detect_batched": (_i, [_vp, _i, _vp, _vp, _sz, _vp]),
+    "ocd_detect_batched_static": (_i, [_vp, _i, _vp, _vp]),
     "ocd_autotune_batched": (_i, [_vp, _i, _vp, _sz, _i, _vp, _vp]),
     "ocd_graph_create_batched": (_i, [_vp, _i, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
     "ocd_graph_launch": (_i, [_vp, _vp]),

@@ -145,6 +145,24 @@ def ocd_detect_batched(cells, tune: Tune | None = None, workspace: torch.Tensor 
     return cells
 
 
+def ocd_detect_batched_static(cells, tune: Tune | None = None,
+                              stream: torch.cuda.Stream | None = None):
+    """ocd_detect_batched with the library's static ticket counters: no
+    workspace and no allocation (outputs must already be in the cells), at
+    most OCD_STATIC_MAX_CELLS cells, and calls on one device must not overlap
+    in time (use one stream).  Make the first call on a device outside CUDA
+    graph capture."""
+    lib = _native.load()
+    arr, dev = _cell_array(cells)
+    if arr is None:
+        return cells
+    with torch.cuda.device(dev):
+        st = lib.ocd_detect_batched_static(arr, len(cells), ctypes.byref(tune._t) if tune else None,
+                                           _stream_handle(stream))
+    _native.check(st)
+    return cells
+
+
 def ocd_autotune_batched(cells, reps: int = 3, workspace: torch.Tensor | None = None,
                          stream: torch.cuda.Stream | None = None) -> Tune:
     """Times the candidate tiles per cell shape on the cells' own buffers

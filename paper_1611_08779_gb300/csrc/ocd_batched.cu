@@ -28,6 +28,10 @@
 
 using namespace ocdh;
 
+// Ticket counters of ocd_detect_batched_static (1 KiB per device): one per
+// launch, and a call makes at most one launch per non-empty cell.
+static __device__ __align__(256) unsigned int g_static_tickets[OCD_STATIC_MAX_CELLS];
+
 namespace {
 
 constexpr int kTmaThreads = 128;
@@ -202,16 +206,11 @@ int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
   return OCD_OK;
 }
 
-int check_batch_args(const ocd_cell_t* cells, int ncells, void* workspace, size_t bytes) {
+// Every cell's arguments, before any CUDA call.
+int check_cells(const ocd_cell_t* cells, int ncells) {
   if (ncells < 0 || ncells > OCD_MAX_CELLS)
     return fail(OCD_ERR_ARG, "ncells=%d outside 0..%d", ncells, OCD_MAX_CELLS);
   if (ncells > 0 && !cells) return fail(OCD_ERR_ARG, "cells must not be NULL");
-  if (ncells > 0 && (!workspace || ((uintptr_t)workspace & 3u)))
-    return fail(OCD_ERR_ARG, "workspace must be a 4-byte aligned device pointer");
-  if (ncells > 0 && bytes < ocd_batched_workspace_size(ncells))
-    return fail(OCD_ERR_ARG, "workspace of %zu bytes is smaller than the %zu needed", bytes,
-                ocd_batched_workspace_size(ncells));
-  // every cell's arguments, before any CUDA call
   for (int i = 0; i < ncells; ++i) {
     const ocd_cell_t& c = cells[i];
     Alphabet al;
@@ -224,6 +223,18 @@ int check_batch_args(const ocd_cell_t* cells, int ncells, void* workspace, size_
     }
   }
   return OCD_OK;
+}
+
+int check_batch_args(const ocd_cell_t* cells, int ncells, void* workspace, size_t bytes) {
+  if (ncells < 0 || ncells > OCD_MAX_CELLS)
+    return fail(OCD_ERR_ARG, "ncells=%d outside 0..%d", ncells, OCD_MAX_CELLS);
+  if (ncells > 0 && !cells) return fail(OCD_ERR_ARG, "cells must not be NULL");
+  if (ncells > 0 && (!workspace || ((uintptr_t)workspace & 3u)))
+    return fail(OCD_ERR_ARG, "workspace must be a 4-byte aligned device pointer");
+  if (ncells > 0 && bytes < ocd_batched_workspace_size(ncells))
+    return fail(OCD_ERR_ARG, "workspace of %zu bytes is smaller than the %zu needed", bytes,
+                ocd_batched_workspace_size(ncells));
+  return check_cells(cells, ncells);
 }
 
 // Enqueues the planned launches: counters zeroed on `stream`, then the
@@ -290,6 +301,29 @@ int run_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
   return st;
 }
 
+struct StaticScratch {
+  bool ready = false;
+  unsigned int* ptr = nullptr;
+};
+StaticScratch g_static[kMaxDevices];
+std::mutex g_static_mu;
+
+// Device address of g_static_tickets on `dev` (the current device), looked
+// up once per device.
+int static_scratch(int dev, unsigned int*& out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(OCD_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static[dev].ready) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_tickets);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    g_static[dev].ptr = static_cast<unsigned int*>(p);
+    g_static[dev].ready = true;
+  }
+  out = g_static[dev].ptr;
+  return OCD_OK;
+}
+
 }  // namespace
 
 struct ocd_graph {
@@ -311,6 +345,22 @@ int ocd_detect_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tu
   int st = check_batch_args(cells, ncells, workspace, workspace_bytes);
   if (st != OCD_OK || ncells == 0) return st;
   return run_batch(cells, ncells, tune, nullptr, workspace, stream);
+}
+
+int ocd_detect_batched_static(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
+                              cudaStream_t stream) {
+  if (ncells > OCD_STATIC_MAX_CELLS)
+    return fail(OCD_ERR_UNSUPPORTED, "ncells=%d exceeds the %d cells of the static scratch", ncells,
+                OCD_STATIC_MAX_CELLS);
+  int st = check_cells(cells, ncells);
+  if (st != OCD_OK || ncells == 0) return st;
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  unsigned int* tickets = nullptr;
+  st = static_scratch(dev, tickets);
+  if (st != OCD_OK) return st;
+  return run_batch(cells, ncells, tune, nullptr, tickets, stream);
 }
 
 int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
