@@ -600,6 +600,93 @@ def run_batched(args):
     return 0
 
 
+def run_unfolded(args):
+    """Differentiable unfolded OCD-BOX: 128x16, K = 5, 4096 (subcarrier,
+    symbol) samples (each its own channel), 16-QAM, SNR uniform in 5-25 dB per
+    sample, BCE loss on the LLRs.  A step is forward + loss + adjoint."""
+    import torch
+    import torch.nn.functional as F
+
+    import paper_1611_08779_gb300 as ocd
+    from paper_1611_08779_gb300 import synth
+    b, u, k, order, nsc = 128, 16, 5, 16, 4096
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(21)
+    snr = rng.uniform(5.0, 25.0, size=nsc)
+    n0 = 10.0 ** (-snr / 10.0)
+    d = synth.make_uplink(nsc, b, u, 1, order, 100.0, seed=21)
+    noise = rng.standard_normal(d["Y"].shape) + 1j * rng.standard_normal(d["Y"].shape)
+    Y = (d["Y"] + noise * np.sqrt(n0 / 2.0)[:, None, None]).astype(np.complex64)
+    H = torch.from_numpy(d["H"]).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    N0 = torch.from_numpy(n0.astype(np.float32)).to(dev)
+    bits = torch.from_numpy(d["bits"].astype(np.float32)).to(dev)
+    om = torch.full((k,), 0.9, device=dev, requires_grad=True)
+    al = torch.full((k,), 0.05, device=dev, requires_grad=True)
+
+    def step():
+        om.grad = None
+        al.grad = None
+        _, llr = ocd.unfolded_ocd(om, al, H, Yd, N0, 1.0, "box", order)
+        loss = F.binary_cross_entropy_with_logits(llr, bits)
+        loss.backward()
+        return loss
+
+    def fwd():
+        with torch.no_grad():
+            ocd.unfolded_ocd(om, al, H, Yd, N0, 1.0, "box", order)
+
+    def timed(fn, steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps
+
+    steps = max(3, min(args.steps, 200))
+    ms_fwd = timed(fwd, steps)
+    sampler = ClockSampler(dev.index)
+    with sampler:
+        ms = timed(step, steps)
+    q = 4
+    samples = nsc
+    # algorithmic work of one step: forward 8BUK + 2BU FMA, adjoint (replay +
+    # reverse) 16BUK + 2BU FMA per sample; bytes: H read twice, Y read, the
+    # checkpoints written and read, xhat / LLR written and read back
+    fma = samples * (24 * b * u * k + 4 * b * u)
+    nbytes = samples * (2 * 8 * b * u + 8 * b + 2 * k * (b + u) * 8 + 2 * (8 * u + 4 * u * q)
+                        + 4 * u * q)
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma_tf = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    t_bound = max(nbytes / (hbm * 1e9), 2.0 * fma / (fma_tf * 1e12))
+    line = {
+        "metric": "training samples/s, unfolded OCD-BOX forward + adjoint (128x16, K=5, 16-QAM)",
+        "workload": "unfolded", "value": samples / (ms / 1e3), "unit": "samples/s", "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "forward_ms": ms_fwd,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic (i.i.d. Rayleigh H, "
+        "Gray 16-QAM, AWGN at SNR uniform 5-25 dB per sample)",
+        "config": {"workload": f"{samples} samples of 128x16, K=5, T=1, BCE loss", "B": b, "U": u,
+                   "K": k, "qam": order, "l2": "inputs 67 MB + checkpoints 24 MB (no flush)"},
+        "roofline": {"bound": "max(hbm, fp32)", "bound_ms": t_bound * 1e3,
+                     "frac": t_bound * 1e3 / ms, "achieved_tflops": 2.0 * fma / (ms / 1e3) / 1e12,
+                     "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_peak": hbm,
+                     "fp32_peak_tflops": fma_tf, "peak_source": f"{src} hbm_gbs; FP32 nominal"},
+        "loss": float(step()),
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,10 +699,11 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["metric", "precision", "batched"], default="metric",
+    ap.add_argument("--workload", choices=["metric", "precision", "batched", "unfolded"], default="metric",
                     help="metric: the headline 128x8 configuration; precision: 256x16 K=4 in "
                          "float32 / bfloat16 / float16 storage with per-SNR accuracy; batched: "
-                         "mixed cells in one persistent launch")
+                         "mixed cells in one persistent launch; unfolded: differentiable OCD-BOX "
+                         "forward + adjoint (128x16, K=5, 4096 samples)")
     ap.add_argument("--cells", type=int, default=24, help="cells of the batched workload")
     ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
                     help="seconds of clock sampling the timed steps are extended to")
@@ -628,6 +716,8 @@ def main(argv=None):
         return run_precision(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "unfolded":
+        return run_unfolded(args)
     return run_ours(args)
 
 
