@@ -25,7 +25,11 @@
 //
 // Layout: one warp per (subcarrier, symbol) sample; lane l holds the
 // residual (and its adjoint) of antennas l + 32 j, j < NA; lane u holds z_u,
-// ||h_u||^2 and the adjoint of z_u.
+// ||h_u||^2 and the adjoint of z_u.  When it fits (U (32 NA + 1) complex per
+// warp, 4 warps within 192 KB), each warp first copies its sample's channel
+// into shared memory, user-major, with coalesced reads, so that every h_u
+// load of the K sweeps (and of the adjoint's replays) is a conflict-free
+// shared load instead of a strided global one.
 #include <cuda_runtime.h>
 
 #include "ocd_common.cuh"
@@ -62,17 +66,39 @@ __device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) 
   p = d * n;
 }
 
+// Column stride (complex elements) of the user-major channel copy in shared
+// memory: 32 NA + 1, so the transposing stores of one warp spread over the
+// banks and the column loads (lane b reads antenna b) are conflict-free.
 template <int NA>
+__host__ __device__ constexpr int staged_stride() { return 32 * NA + 1; }
+
+template <int NA, bool SMEM>
 struct Warp {
   const UnfoldParams& P;
-  const float2* Hw;  // channel of this sample's subcarrier, [B][U]
+  const float2* Hw;  // channel of this sample's subcarrier, [B][U] in global memory
+  float2* sH;        // SMEM: this warp's user-major copy [U][staged_stride], zero padded
   int lane;
+
+  // Copies H[w] into sH (coalesced reads, transposed stores).
+  __device__ __forceinline__ void stage() const {
+    if (!SMEM) return;
+    constexpr int st = staged_stride<NA>();
+    __syncwarp();  // the previous sample's reads are done
+    const int n = P.B * P.U;
+    for (int e = lane; e < n; e += 32) {
+      const int b = e / P.U;
+      const int u = e - b * P.U;
+      sH[u * st + b] = __ldg(Hw + e);
+    }
+    __syncwarp();
+  }
 
   __device__ __forceinline__ void load_h(int u, float2 (&h)[NA]) const {
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
       const int b = lane + 32 * j;
-      h[j] = b < P.B ? __ldg(Hw + (long long)b * P.U + u) : make_float2(0.0f, 0.0f);
+      if (SMEM) h[j] = sH[u * staged_stride<NA>() + b];  // antennas >= B hold zeros
+      else h[j] = b < P.B ? __ldg(Hw + (long long)b * P.U + u) : make_float2(0.0f, 0.0f);
     }
   }
 
@@ -129,16 +155,23 @@ struct Warp {
   }
 };
 
-template <int NA>
+template <int NA, bool SMEM>
 __global__ void __launch_bounds__(128)
 ocd_unfolded_forward_kernel(const __grid_constant__ UnfoldParams P) {
+  extern __shared__ float2 unf_smem[];
   const int lane = threadIdx.x & 31;
+  float2* sH = unf_smem + (threadIdx.x >> 5) * P.U * staged_stride<NA>();
+  if (SMEM) {
+    // padding antennas (b >= B) stay zero: staging writes only b < B
+    for (int i = lane; i < P.U * staged_stride<NA>(); i += 32) sH[i] = make_float2(0.0f, 0.0f);
+  }
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   const int stride = P.B + P.U;
   for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.samples;
        s += nw) {
     const long long w = s / P.T;
-    Warp<NA> W{P, P.H + w * P.B * P.U, lane};
+    Warp<NA, SMEM> W{P, P.H + w * P.B * P.U, sH, lane};
+    W.stage();
     const float nrm = W.norms();
     float2 r[NA];
 #pragma unroll
@@ -175,18 +208,22 @@ ocd_unfolded_forward_kernel(const __grid_constant__ UnfoldParams P) {
 // dimension): L_b = rho (min_{bit b = 0} (x - v)^2 - min_{bit b = 1} (x - v)^2)
 // is linear in x between changes of the minimizing levels v0*, v1*, with
 // slope 2 rho (v1* - v0*).
-__device__ __forceinline__ float dimension_llr_slope(float x, float rho, const DetectParams& D,
-                                                     const float* g) {
-  const int nb = D.nb, M = D.M;
-  float b0[4], b1[4], v0[4], v1[4];
-  for (int j = 0; j < nb; ++j) { b0[j] = FLT_MAX; b1[j] = FLT_MAX; v0[j] = 0.0f; v1[j] = 0.0f; }
+template <int NB>
+__device__ __forceinline__ float dimension_llr_slope_nb(float x, float rho, float step,
+                                                        const float* g) {
+  constexpr int M = 1 << NB;
+  float b0[NB], b1[NB], v0[NB], v1[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) { b0[j] = FLT_MAX; b1[j] = FLT_MAX; v0[j] = 0.0f; v1[j] = 0.0f; }
+#pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float v = (float)(2 * i + 1 - M) * D.lvl_step;
+    const float v = (float)(2 * i + 1 - M) * step;
     const float e = x - v;
     const float dd = e * e;
     const int gw = i ^ (i >> 1);
-    for (int j = 0; j < nb; ++j) {
-      if ((gw >> (nb - 1 - j)) & 1) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if ((gw >> (NB - 1 - j)) & 1) {
         if (dd < b1[j]) { b1[j] = dd; v1[j] = v; }
       } else {
         if (dd < b0[j]) { b0[j] = dd; v0[j] = v; }
@@ -194,21 +231,39 @@ __device__ __forceinline__ float dimension_llr_slope(float x, float rho, const D
     }
   }
   float s = 0.0f;
-  for (int j = 0; j < nb; ++j) s = fmaf(g[j], 2.0f * rho * (v1[j] - v0[j]), s);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) s = fmaf(g[j], 2.0f * rho * (v1[j] - v0[j]), s);
   return s;
 }
 
-template <int NA>
+__device__ __forceinline__ float dimension_llr_slope(float x, float rho, const DetectParams& D,
+                                                     const float* g) {
+  switch (D.nb) {
+    case 1: return dimension_llr_slope_nb<1>(x, rho, D.lvl_step, g);
+    case 2: return dimension_llr_slope_nb<2>(x, rho, D.lvl_step, g);
+    case 3: return dimension_llr_slope_nb<3>(x, rho, D.lvl_step, g);
+    default: return dimension_llr_slope_nb<4>(x, rho, D.lvl_step, g);
+  }
+}
+
+template <int NA, bool SMEM>
 __global__ void __launch_bounds__(128)
 ocd_unfolded_backward_kernel(const __grid_constant__ UnfoldParams P) {
+  extern __shared__ float2 unf_smem[];
   const int lane = threadIdx.x & 31;
+  float2* sH = unf_smem + (threadIdx.x >> 5) * P.U * staged_stride<NA>();
+  if (SMEM) {
+    // padding antennas (b >= B) stay zero: staging writes only b < B
+    for (int i = lane; i < P.U * staged_stride<NA>(); i += 32) sH[i] = make_float2(0.0f, 0.0f);
+  }
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   const int stride = P.B + P.U;
   const int K = P.K;
   for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.samples;
        s += nw) {
     const long long w = s / P.T;
-    Warp<NA> W{P, P.H + w * P.B * P.U, lane};
+    Warp<NA, SMEM> W{P, P.H + w * P.B * P.U, sH, lane};
+    W.stage();
     const float nrm = W.norms();
     // ---- adjoint of the soft output and of xhat (lane u)
     float2 zbar = make_float2(0.0f, 0.0f);
@@ -325,10 +380,22 @@ ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples,
   }
 }
 
+constexpr size_t kUnfoldedSmemLimit = 192 * 1024;  // per CTA of 4 warps
+
 template <int NA>
 cudaError_t launch_pair(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
-  if (backward) ocd_unfolded_backward_kernel<NA><<<grid, 128, 0, stream>>>(P);
-  else ocd_unfolded_forward_kernel<NA><<<grid, 128, 0, stream>>>(P);
+  const size_t smem = 4ull * P.U * staged_stride<NA>() * sizeof(float2);
+  if (smem <= kUnfoldedSmemLimit) {
+    const void* fn = backward ? reinterpret_cast<const void*>(ocd_unfolded_backward_kernel<NA, true>)
+                              : reinterpret_cast<const void*>(ocd_unfolded_forward_kernel<NA, true>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (backward) ocd_unfolded_backward_kernel<NA, true><<<grid, 128, smem, stream>>>(P);
+    else ocd_unfolded_forward_kernel<NA, true><<<grid, 128, smem, stream>>>(P);
+  } else {
+    if (backward) ocd_unfolded_backward_kernel<NA, false><<<grid, 128, 0, stream>>>(P);
+    else ocd_unfolded_forward_kernel<NA, false><<<grid, 128, 0, stream>>>(P);
+  }
   return cudaGetLastError();
 }
 
