@@ -42,7 +42,7 @@ FALLBACK_HBM_GBS = 6800.0
 SMS_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
-KERNEL_SOURCES = ["ocd_common.cuh", "ocd_projected_tma.cuh", "ocd_projected_tma.cu"]
+KERNEL_SOURCES = ["ocd_common.cuh", "ocd_mma.cuh", "ocd_projected_tma.cuh", "ocd_projected_tma.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ocd_projected_tma_128x8_t14_k3.md")
 MIN_CLOCK_WINDOW_S = 0.5
 REF_BUDGET_S = 60.0
@@ -503,15 +503,15 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
     return 0
 
-def batched_bound_s(spec, hbm_gbs, fma_tflops):
-    """Roofline time of one cell in the arrangement the batched form gives it:
-    the projected form (U <= 16, T >= 2) is bound by HBM; the residual form by
-    max(HBM, FP32 FMA: 8BU per sweep and symbol, Section III-B)."""
+def batched_bound_s(spec, hbm_gbs, fma_tflops, projected):
+    """Roofline time of one cell in the arrangement the batched form runs it
+    in: the projected form is bound by HBM; the residual form by max(HBM,
+    FP32 FMA: 8BU per sweep and symbol, Section III-B)."""
     b, u, t, k = spec["B"], spec["U"], spec["T"], spec["K"]
     q = int(round(math.log2(spec["order"])))
     nbytes = algorithmic_bytes_per_sc(b, u, t, q) * spec["Nsc"]
     t_hbm = nbytes / (hbm_gbs * 1e9)
-    if u <= 16 and t >= 2:
+    if projected:
         return t_hbm, nbytes
     t_alu = 2.0 * algorithmic_fma_per_sc(b, u, t, k) * spec["Nsc"] / (fma_tflops * 1e12)
     return max(t_hbm, t_alu), nbytes
@@ -540,9 +540,6 @@ def run_batched(args):
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fma_tf = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    bound = [batched_bound_s(s, hbm, fma_tf) for s in specs]
-    t_bound = sum(b for b, _ in bound)
-    nbytes = sum(n for _, n in bound)
     ws = ocd.make_workspace(len(cells), dev)
 
     def per_cell():
@@ -569,6 +566,10 @@ def run_batched(args):
     t0 = time.perf_counter()
     tune = ocd.ocd_autotune_batched(cells, reps=2, workspace=ws)
     tune_s = time.perf_counter() - t0
+    algo_of = {(e["B"], e["U"], e["T"]): e["algo"] for e in tune.entries}
+    bound = [batched_bound_s(s, hbm, fma_tf, algo_of[(s["B"], s["U"], s["T"])] == 2) for s in specs]
+    t_bound = sum(b for b, _ in bound)
+    nbytes = sum(n for _, n in bound)
     arms["batched_tuned"] = timed(lambda: ocd.ocd_detect_batched(cells, tune=tune, workspace=ws), steps)
     graph = ocd.BatchedGraph(cells, tune=tune, workspace=ws)
     sampler = ClockSampler(dev.index)
@@ -589,7 +590,8 @@ def run_batched(args):
                    "l2": "inputs larger than L2 (no flush)"},
         "arms_gbps": {k: bits / (v / 1e3) / 1e9 for k, v in arms.items()},
         "arms_ms": arms,
-        "roofline": {"bound": "mixed (hbm for projected cells, max(hbm, fp32) for residual cells)",
+        "roofline": {"bound": "mixed (hbm for cells the tuned plan runs in the projected form, "
+                              "max(hbm, fp32) for residual-form cells)",
                      "bound_ms": t_bound * 1e3, "frac": t_bound * 1e3 / ms,
                      "hbm_achieved_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_peak": hbm,
                      "fp32_peak_tflops": fma_tf, "peak_source": f"{src} hbm_gbs; FP32 nominal"},

@@ -55,11 +55,12 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *   OCD_ALGO_PROJECTED  r carried as q = H^H r (U entries per symbol):
  *                       q0 = H^H y and G = H^H H once per subcarrier, then
  *                       h_u^H r = q_u and r -= h_u dz becomes q -= G[:,u] dz.
- *                       Supports U <= 8 always, and U <= 16 when H and Y
- *                       are 16-byte aligned with even B (float32 storage)
- *                       or B % 4 == 0 (16-bit storage).
- *   OCD_ALGO_AUTO       PROJECTED when it supports the shape and T >= 2,
- *                       else RESIDUAL.
+ *                       Supports U <= 8 always; U <= 16 when H and Y are
+ *                       16-byte aligned with even B (float32 storage) or
+ *                       B % 4 == 0 (16-bit storage); U <= 32 with float32
+ *                       storage, even B and 16-byte aligned H and Y.
+ *   OCD_ALGO_AUTO       PROJECTED when it supports the shape and T >= 2 (or
+ *                       U > 16), else RESIDUAL.
  */
 typedef enum { OCD_ALGO_AUTO = 0, OCD_ALGO_RESIDUAL = 1, OCD_ALGO_PROJECTED = 2 } ocd_algo_t;
 

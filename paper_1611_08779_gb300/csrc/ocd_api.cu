@@ -11,6 +11,7 @@
 
 #include "ocd.h"
 #include "ocd_common.cuh"
+#include "ocd_batch.cuh"
 #include "ocd_host.h"
 #include "ocd_residual.cuh"
 
@@ -117,6 +118,11 @@ int device_info(int dev, DeviceInfo& out) {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
+    for (const void* fn : {ocd::projected_wide_kernel_ptr(),
+                           reinterpret_cast<const void*>(ocd::batched_wide_kernel())}) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
     g_dev[dev].sms = sms;
     g_dev[dev].smem_optin = (size_t)optin;
     g_dev[dev].ready = true;
@@ -203,15 +209,21 @@ bool can_h16(const ocd::DetectParams& P) {
   return P.storage != ocd::kStoreC64 && P.U <= ocd::kH16MaxUsers && P.B % 4 == 0 &&
          aligned16(P);
 }
+bool can_wide(const ocd::DetectParams& P) {
+  return P.storage == ocd::kStoreC64 && P.U > ocd::kTmaMaxUsers && P.U <= ocd::kWideMaxUsers &&
+         P.B % 2 == 0 && aligned16(P);
+}
 bool can_projected(const ocd::DetectParams& P) {
-  return can_tma32(P) || can_h16(P) || P.U <= ocd::kProjectedMaxUsers;
+  return can_tma32(P) || can_wide(P) || can_h16(P) || P.U <= ocd::kProjectedMaxUsers;
 }
 
 // Algorithm choice for OCD_ALGO_AUTO: the projected form wins whenever its
 // two per-subcarrier products are shared by more than one symbol.
+// Above 16 users the residual form's staged channel leaves the SMs nearly
+// idle, so the (four-tile) projected form wins even for one symbol.
 int resolve_algo(int algo, const ocd::DetectParams& P) {
   if (algo != OCD_ALGO_AUTO) return algo;
-  return (can_projected(P) && P.T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  return (can_projected(P) && (P.T >= 2 || can_wide(P))) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
 }
 
 int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
@@ -219,6 +231,21 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   const long long need = (P.Nsc + nt / 32 - 1) / (nt / 32);  // one warp per subcarrier
   int per_sm = 0;
   cudaError_t e;
+  if (can_wide(P)) {
+    const void* fn = ocd::projected_wide_kernel_ptr();
+    const int wt = ocd::projected_wide_threads();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wt,
+                                                      ocd::projected_wide_smem_per_cta());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm >= 1) {
+      long long grid = (long long)di.sms * per_sm;
+      if (grid > P.Nsc) grid = P.Nsc;  // one warp (CTA) per subcarrier
+      e = ocd::launch_projected_wide(P, (unsigned)grid, stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) return OCD_OK;
+      if (e != cudaErrorNotSupported) return cuda_fail(e, "projected kernel launch");
+    }
+  }
   const bool h16 = can_h16(P);
   if (can_tma32(P) || h16) {
     const void* fn =
@@ -240,7 +267,8 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   }
   if (U > ocd::kProjectedMaxUsers)
     return fail(OCD_ERR_UNSUPPORTED, "projected form for U=%d needs the bulk-copy path "
-                "(even B, or B %% 4 == 0 for 16-bit storage; 16-byte aligned H and Y)", U);
+                "(even B, or B %% 4 == 0 for 16-bit storage; 16-byte aligned H and Y; "
+                "float32 storage above 16 users)", U);
   const int umax = U <= 4 ? 4 : 8;
   KernelFn fn = ocd::projected_kernel(umax);
   const size_t smem = (nt / 32) * ocd::projected_smem_per_warp(umax);
@@ -456,11 +484,12 @@ int ocd_wait_selftest(int limit_us, cudaStream_t stream) {
 }
 
 int ocd_fault_status(int clear) {
-  unsigned int bits = 0, bits16 = 0;
+  unsigned int bits = 0, bits16 = 0, bitsw = 0;
   cudaError_t e = ocd::projected_tma_fault(&bits, clear != 0);
   if (e == cudaSuccess) e = ocd::projected_h16_fault(&bits16, clear != 0);
+  if (e == cudaSuccess) e = ocd::projected_wide_fault(&bitsw, clear != 0);
   if (e != cudaSuccess) return cuda_fail(e, "reading the fault word");
-  return (int)(bits | bits16);
+  return (int)(bits | bits16 | bitsw);
 }
 
 const char* ocd_last_error(void) { return g_err; }

@@ -49,4 +49,14 @@ cudaError_t encode_ymap(const DetectParams& P, CUtensorMap* map);
 // bulk-copy kernels.
 int tma_steps_per_sc(int B, int T);
 
+// Bulk-copy projected form for 16 < U <= 32 (float32 storage, even B,
+// 16-byte aligned H and Y): one warp per CTA.
+constexpr int kWideMaxUsers = 32;
+const void* projected_wide_kernel_ptr();
+size_t projected_wide_smem_per_cta();
+int projected_wide_threads();
+cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStream_t stream);
+BatchFn batched_wide_kernel();
+cudaError_t projected_wide_fault(unsigned int* bits, bool clear);
+
 }  // namespace ocd

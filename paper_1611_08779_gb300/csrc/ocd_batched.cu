@@ -70,23 +70,25 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   build_params(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode, al, c.xhat,
                c.llr, cp.P);
   const ocd_tune_entry_t* te = force ? force : find_tune(tune, c);
-  const bool tma_ok = can_tma32(cp.P);
+  const bool wide = can_wide(cp.P);
+  const bool tma_ok = can_tma32(cp.P) || wide;
   int algo = c.algo;
   if (algo == OCD_ALGO_AUTO && te && (te->algo == OCD_ALGO_RESIDUAL || te->algo == OCD_ALGO_PROJECTED))
     algo = te->algo;
-  if (algo == OCD_ALGO_AUTO) algo = (tma_ok && c.T >= 2) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  if (algo == OCD_ALGO_AUTO)
+    algo = (tma_ok && (c.T >= 2 || wide)) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
   if (algo == OCD_ALGO_PROJECTED && !tma_ok)
-    return fail(OCD_ERR_UNSUPPORTED, "batched projected form needs float32 storage, U <= 16, "
-                "even B and 16-byte aligned H and Y (U=%d B=%d)", c.U, c.B);
+    return fail(OCD_ERR_UNSUPPORTED, "batched projected form needs float32 storage, even B "
+                "and 16-byte aligned H and Y (U=%d B=%d)", c.U, c.B);
   if (algo == OCD_ALGO_PROJECTED) {
     cp.kind = 1;
-    cp.ut = c.U <= 8 ? 1 : 2;
+    cp.ut = c.U <= 8 ? 1 : c.U <= 16 ? 2 : 4;
     cp.npp = cp.S = 0;
-    cp.nt = kTmaThreads;
-    cp.smem = ocd::projected_tma_smem_per_cta(c.U);
+    cp.nt = wide ? ocd::projected_wide_threads() : kTmaThreads;
+    cp.smem = wide ? ocd::projected_wide_smem_per_cta() : ocd::projected_tma_smem_per_cta(c.U);
     int spt = te && te->sc_per_ticket > 0 ? te->sc_per_ticket : 0;
     if (spt == 0) {
-      const int steps = ocd::tma_steps_per_sc(c.B, c.T);
+      const int steps = ocd::tma_steps_per_sc(c.B, c.T) + (wide ? (c.B + 31) / 32 : 0);
       spt = (kDefaultStepsPerTicket + steps - 1) / steps;
     }
     if (spt < 1 || spt > 256) return fail(OCD_ERR_ARG, "sc_per_ticket=%d outside 1..256", spt);
@@ -165,8 +167,9 @@ int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
       L.tab.reset(new ocd::BatchTable);
       memset(L.tab.get(), 0, sizeof(ocd::BatchTable));
       const CellPlan& f = plans[fam[a]];
-      L.fn = f.kind == 1 ? reinterpret_cast<const void*>(ocd::batched_tma_kernel(f.ut == 1 ? 8 : 16))
-                         : reinterpret_cast<const void*>(ocd::batched_residual_kernel(f.npp, f.S));
+      L.fn = f.kind == 0 ? reinterpret_cast<const void*>(ocd::batched_residual_kernel(f.npp, f.S))
+             : f.ut == 4 ? reinterpret_cast<const void*>(ocd::batched_wide_kernel())
+                         : reinterpret_cast<const void*>(ocd::batched_tma_kernel(f.ut == 1 ? 8 : 16));
       L.nt = f.nt;
       L.smem = 0;
       L.work = 0.0;
@@ -419,12 +422,12 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
     build_params(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode, al, c.xhat,
                  c.llr, P);
     const ocd_tune_entry_t base = {c.B, c.U, c.T, c.storage, 0, 0, 0, 0, 0.0f};
-    bool tma_all = can_tma32(P);
+    bool tma_all = can_tma32(P) || can_wide(P);
     for (const ocd_cell_t& g : group) {
       ocd::DetectParams Pg;
       build_params(g.H, g.Y, g.storage, g.Nsc, g.B, g.U, g.T, g.N0, g.Es, g.K, g.mode, al,
                    g.xhat, g.llr, Pg);
-      tma_all = tma_all && can_tma32(Pg);
+      tma_all = tma_all && (can_tma32(Pg) || can_wide(Pg));
     }
     if (tma_all && c.T >= 1) {
       for (int spt : {1, 2, 4, 8, 16, 32}) {

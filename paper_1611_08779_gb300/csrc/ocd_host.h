@@ -50,7 +50,8 @@ struct Plan {
 int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl, int S_req,
               int L_req);
 
-bool can_tma32(const ocd::DetectParams& P);
+bool can_tma32(const ocd::DetectParams& P);  // U <= 16
+bool can_wide(const ocd::DetectParams& P);   // 16 < U <= 32
 
 // Internal streams (per device, created once) shared by the host-buffer path
 // and the batched form; the caller holds g_hs_mu for the whole enqueue.

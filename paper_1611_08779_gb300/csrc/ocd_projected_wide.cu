@@ -1,0 +1,36 @@
+// Bulk-copy projected OCD kernels for up to 32 users: launch, the batched
+// kernel pointer and the fault word.
+#include "ocd_projected_wide.cuh"
+
+namespace ocd {
+
+const void* projected_wide_kernel_ptr() {
+  return reinterpret_cast<const void*>(ocd_projected_wide_kernel);
+}
+
+size_t projected_wide_smem_per_cta() { return WideShape::kWarpBytes + 1024; }
+
+int projected_wide_threads() { return WideShape::kThreads; }
+
+cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStream_t stream) {
+  CUtensorMap map;
+  const cudaError_t e = encode_ymap(P, &map);
+  if (e != cudaSuccess) return e;
+  DetectParams p = P;
+  void* args[] = {&p, &map};
+  return cudaLaunchKernel(projected_wide_kernel_ptr(), dim3(grid), dim3(WideShape::kThreads), args,
+                          projected_wide_smem_per_cta(), stream);
+}
+
+BatchFn batched_wide_kernel() { return ocd_batched_wide_kernel; }
+
+cudaError_t projected_wide_fault(unsigned int* bits, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(bits, g_wide_fault, sizeof(unsigned int));
+  if (e == cudaSuccess && clear) {
+    const unsigned int zero = 0;
+    e = cudaMemcpyToSymbol(g_wide_fault, &zero, sizeof(unsigned int));
+  }
+  return e;
+}
+
+}  // namespace ocd

@@ -1,0 +1,450 @@
+// Projected-residual OCD for up to 32 users (four 8-user tiles), channel
+// and received vectors staged by the bulk-copy (TMA) engine.  Same algebra
+// as ocd_projected_tma.cuh (q = H^H r; q0 = H^H Y^T and G = H^H H once per
+// subcarrier on the tensor cores, then the K sweeps on q), with the work of
+// one subcarrier split into phases so that one warp's accumulators stay
+// within the register file:
+//
+//   G phase  (one step per 32-antenna block): only the channel block is
+//            staged; the 10 tiles (m, n), n >= m, of G are accumulated.  At
+//            the last block G goes to shared memory (Hermitian fill) with the
+//            preprocessing of Algorithm 1.
+//   q0 pass p (one step per block, per 16 symbols): channel block and the
+//            received rows; the 8 tiles of q0 (4 user tiles x 2 symbol
+//            tiles) are accumulated in the same registers; at the last block
+//            the K sweeps run on q and the outputs are written.
+//
+// Each accumulator tile keeps two parts, hi*hi and hi*lo + lo*hi of the
+// three-term TF32 split, summed once per phase.  One warp per CTA (the
+// per-warp staging, q, G and preprocessing areas take 37 KB of shared
+// memory); the channel block is therefore read once per phase, the second
+// time from L2.
+#pragma once
+
+#include <cuda.h>  // CUtensorMap (type only; no driver library is linked)
+
+#include <type_traits>
+
+#include "ocd_batch.cuh"
+#include "ocd_common.cuh"
+#include "ocd_mma.cuh"
+#include "ocd_tma_util.cuh"
+
+namespace ocd {
+
+#ifndef OCD_WIDE_STAGES
+#define OCD_WIDE_STAGES 2     // staging buffers per warp
+#endif
+
+struct WideShape {
+  static constexpr int kUsers = 32;                         // user slots (4 MMA tiles)
+  static constexpr int kPass = 16;                          // symbols per q0 pass
+  static constexpr int kBB = 32;                            // antennas per staged block
+  static constexpr int kBoxAnt = 16;                        // antennas per Y box (128 B rows)
+  static constexpr int kBoxBytes = kPass * 128;
+  static constexpr int kBoxes = kBB / kBoxAnt;
+  static constexpr int kYBytes = kBoxes * kBoxBytes;
+  static constexpr int kHBytes = kBB * kUsers * 8;
+  static constexpr int kBufBytes = kYBytes + kHBytes;       // multiple of 1024
+  static constexpr int kStages = OCD_WIDE_STAGES;
+  static constexpr int kUP = kUsers / 2;                    // users per sweep lane
+  static constexpr int kOffQ = kStages * kBufBytes;         // q0, later z [pass symbol][u]
+  static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;  // G [i][j]
+  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
+  static constexpr int kOffBar = kOffPre + 16 * kUsers;
+  static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
+  static constexpr int kThreads = 32;                       // one warp per CTA
+  static_assert(kBufBytes % 1024 == 0, "swizzled boxes need 1024-byte alignment");
+};
+
+// Fault word of the wide kernels (bit 0: a wait timed out; bit 1: a batched
+// cell's tensor map was misaligned).  Defined here because exactly one
+// translation unit (ocd_projected_wide.cu) includes this header.
+__device__ unsigned int g_wide_fault = 0;
+
+// Index of G tile (m, n), n >= m, among the 10 upper tiles.
+__host__ __device__ constexpr int wide_gtile(int m, int n) { return m * 4 - m * (m - 1) / 2 + (n - m); }
+
+// Two-part split product: d[0] += hi*hi, d[1] += hi*lo + lo*hi.
+__device__ __forceinline__ void mma2_tf32(float (&d)[2][4], const uint32_t (&ah)[3],
+                                          const uint32_t (&al)[3], uint32_t bh0, uint32_t bh1,
+                                          uint32_t bl0, uint32_t bl1) {
+  mma_tf32(d[0], ah[0], ah[1], ah[2], bh0, bh1);
+  mma_tf32(d[1], ah[0], ah[1], ah[2], bl0, bl1);
+  mma_tf32(d[1], al[0], al[1], al[2], bh0, bh1);
+}
+
+// One warp's walk over subcarriers first, first + stride, ... (< end) of
+// problem P (ymap: Y as [Nsc*T][2B] floats, box 32 x 16, 128-byte swizzle).
+// Staging area and barriers persist across calls as in tma_walk; returns
+// false when a wait timed out.
+__device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorMap* ymap,
+                                          unsigned char* ws, uint32_t bar0, uint32_t& parity,
+                                          long long first, long long end, long long stride) {
+  using S = WideShape;
+  constexpr int BB = S::kBB;
+  constexpr int UP = S::kUP;
+  constexpr int NU = S::kUsers;
+  const int lane = threadIdx.x & 31;
+  float* sq = reinterpret_cast<float*>(ws + S::kOffQ);
+  float* sg = reinterpret_cast<float*>(ws + S::kOffG);
+  float* spre = reinterpret_cast<float*>(ws + S::kOffPre);
+
+  const int U = P.U;
+  const int B = P.B;
+  const int T = P.T;
+  const int gq = lane >> 2;
+  const int t = lane & 3;
+  // antenna order inside a k-step and swizzled Y offsets as in tma_walk
+  const int ta = ((t >> 1) << 3) | (t & 1);
+  int yoff[4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    yoff[kk] = gq * 128 + (((kk | ((t >> 1) << 2)) ^ gq) << 4) + ((t & 1) << 3);
+  const int nblk = (B + BB - 1) / BB;
+  const int npasses = (T + S::kPass - 1) / S::kPass;
+  const long long steps_per_sc = (long long)(npasses + 1) * nblk;
+  const long long my_nsc = first < end ? (end - 1 - first) / stride + 1 : 0;
+  const long long nsteps = my_nsc * steps_per_sc;
+  if (nsteps == 0) return true;
+
+  // Step cursor: (subcarrier, phase, block); phase 0 = G, phase p >= 1 =
+  // q0 pass p - 1.
+  struct Cursor {
+    long long sc;
+    int phase, blk;
+  };
+  auto advance = [&](Cursor& q) {
+    if (++q.blk == nblk) {
+      q.blk = 0;
+      if (++q.phase == npasses + 1) {
+        q.phase = 0;
+        q.sc += stride;
+      }
+    }
+  };
+  auto issue = [&](const Cursor& q, int buf) {
+    const int b0 = q.blk * BB;
+    const int bb = min(BB, B - b0);
+    const uint32_t bar = bar0 + 8 * buf;
+    unsigned char* bp = ws + buf * S::kBufBytes;
+    const int nbox = q.phase == 0 ? 0 : (bb + S::kBoxAnt - 1) / S::kBoxAnt;
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nbox * S::kBoxBytes + bb * U * 8));
+    __syncwarp();
+    fence_proxy_async();
+    if (lane < nbox)
+      tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), ymap, 2 * (b0 + S::kBoxAnt * lane),
+                  (int)(q.sc * T + (q.phase - 1) * S::kPass), bar);
+    if (lane == 31) {
+      const float2* src = P.H + (q.sc * (long long)B + b0) * U;
+      bulk_g2s(smem_addr(bp + S::kYBytes), src, (uint32_t)(bb * U * 8), bar);
+    }
+  };
+
+  // acc[i]: G tile i (G phase) or q0 tile 2m + n (q0 passes); rows 0-7 real
+  // and 8-15 imaginary parts of user m*8 + gq.
+  float acc[10][2][4];
+
+  Cursor cur{first, 0, 0};
+  Cursor nxt{first, 0, 0};
+  int buf = 0, ibuf = 0;
+  for (int i = 0; i < S::kStages - 1 && i < nsteps; ++i) {
+    issue(nxt, ibuf);
+    advance(nxt);
+    ibuf = ibuf + 1 == S::kStages ? 0 : ibuf + 1;
+  }
+  for (long long s = 0; s < nsteps; ++s) {
+    if (s + S::kStages - 1 < nsteps) {
+      issue(nxt, ibuf);
+      advance(nxt);
+      ibuf = ibuf + 1 == S::kStages ? 0 : ibuf + 1;
+    }
+    if (!mbar_wait(bar0 + 8 * buf, (parity >> buf) & 1, P.wait_ns)) {
+      if (lane == 0) atomicOr(&g_wide_fault, 1u);
+      for (int i = 1; i < S::kStages; ++i) {
+        if (s + i < nsteps) {
+          const int bi = (buf + i) % S::kStages;
+          mbar_wait(bar0 + 8 * bi, (parity >> bi) & 1, P.wait_ns);
+        }
+      }
+      return false;
+    }
+    parity ^= 1u << buf;
+
+    const long long sc = cur.sc;
+    const int phase = cur.phase;
+    const int blk = cur.blk;
+    const int bb = min(BB, B - blk * BB);
+    const int tb = (phase - 1) * S::kPass;
+    const int np = phase == 0 ? 0 : min(S::kPass, T - tb);
+    const int this_buf = buf;
+    advance(cur);
+    buf = buf + 1 == S::kStages ? 0 : buf + 1;
+    const unsigned char* bp = ws + this_buf * S::kBufBytes;
+    const float2* sH = reinterpret_cast<const float2*>(bp + S::kYBytes);
+
+    if (blk == 0) {
+#pragma unroll
+      for (int i = 0; i < 10; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[i][q][e] = 0.0f;
+    }
+
+    // ---------------- products on the tensor cores ------------------------
+    // Lane (gq, t) holds h_{a_t, m*8+gq} of the four user tiles; antennas
+    // past bb and users past U are masked to zero.
+    const float2* hl = sH + ta * U + gq;
+    const bool full = bb == BB && U == NU;
+    auto split_h = [&](const float2 (&h)[4], uint32_t (&ah)[4][3], uint32_t (&al)[4][3]) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        split_tf32(h[m].x, ah[m][0], al[m][0]);  // a0 = a3 = Re h
+        split_tf32(h[m].y, ah[m][2], al[m][2]);  // a2 = Im h
+        ah[m][1] = ah[m][2] ^ 0x80000000u;       // a1 = -Im h
+        al[m][1] = al[m][2] ^ 0x80000000u;
+      }
+    };
+    auto load_h = [&](int a0, bool ok, float2 (&h)[4]) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const bool okm = full || (ok && m * 8 + gq < U);
+        h[m] = okm ? hl[a0 * U + m * 8] : make_float2(0.0f, 0.0f);
+      }
+    };
+    if (phase == 0) {
+      for (int box = 0; box * S::kBoxAnt < bb; ++box) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int a0 = box * S::kBoxAnt + 2 * kk;
+          float2 h[4];
+          load_h(a0, a0 + ta < bb, h);
+          uint32_t ah[4][3], al[4][3];
+          split_h(h, ah, al);
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int n = m; n < 4; ++n)
+              mma2_tf32(acc[wide_gtile(m, n)], ah[m], al[m], ah[n][0], ah[n][2], al[n][0],
+                        al[n][2]);
+        }
+      }
+    } else {
+      for (int box = 0; box * S::kBoxAnt < bb; ++box) {
+        const unsigned char* yb = bp + box * S::kBoxBytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int a0 = box * S::kBoxAnt + 2 * kk;
+          float2 h[4];
+          load_h(a0, a0 + ta < bb, h);
+          uint32_t ah[4][3], al[4][3];
+          split_h(h, ah, al);
+          const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
+          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
+          uint32_t bh0, bl0, bh1, bl1, ch0, cl0, ch1, cl1;
+          split_tf32(ya.x, bh0, bl0);
+          split_tf32(ya.y, bh1, bl1);
+          split_tf32(yc.x, ch0, cl0);
+          split_tf32(yc.y, ch1, cl1);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            mma2_tf32(acc[2 * m], ah[m], al[m], bh0, bh1, bl0, bl1);
+            mma2_tf32(acc[2 * m + 1], ah[m], al[m], ch0, ch1, cl0, cl1);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (blk != nblk - 1) continue;
+
+    if (phase == 0) {
+      // ---------------- G epilogue: Hermitian fill and preprocessing ------
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int n = m; n < 4; ++n)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float (&a)[2][4] = acc[wide_gtile(m, n)];
+            const float re = a[1][e] + a[0][e];
+            const float im = a[1][2 + e] + a[0][2 + e];
+            const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
+            sg[2 * (i * NU + j)] = re;
+            sg[2 * (i * NU + j) + 1] = im;
+            if (n != m) {
+              sg[2 * (j * NU + i)] = re;
+              sg[2 * (j * NU + i) + 1] = -im;
+            }
+          }
+      __syncwarp();
+      {
+        const float nrm = sg[2 * (lane * NU + lane)];
+        const float den = nrm + P.alpha;
+        const float dinv = (lane < U && den > 0.0f) ? 1.0f / den : 0.0f;
+        const float p = dinv * nrm;
+        spre[4 * lane] = dinv;
+        spre[4 * lane + 1] = p;
+        spre[4 * lane + 2] = nrm;
+        spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
+        sg[2 * (lane * NU + lane) + 1] = 0.0f;  // G_uu is real
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // ---------------- q0 epilogue, sweeps, outputs ------------------------
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int ts = 8 * n + 2 * t + e;
+          const int u = m * 8 + gq;
+          const float (&a)[2][4] = acc[2 * m + n];
+          sq[2 * (ts * NU + u)] = a[1][e] + a[0][e];
+          sq[2 * (ts * NU + u) + 1] = a[1][2 + e] + a[0][2 + e];
+        }
+    __syncwarp();
+    {
+      // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts
+      const int ts = lane >> 1;
+      const int hf = lane & 1;
+      const bool act = ts < np;
+      float qr[UP], qi[UP], zr[UP], zi[UP];
+#pragma unroll
+      for (int l = 0; l < UP; ++l) {
+        const int j = hf * UP + l;
+        qr[l] = act ? sq[2 * (ts * NU + j)] : 0.0f;
+        qi[l] = act ? sq[2 * (ts * NU + j) + 1] : 0.0f;
+        zr[l] = 0.0f;
+        zi[l] = 0.0f;
+      }
+      const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
+      const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
+      for (int k = 0; k < P.K; ++k) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          if (u < U) {
+            const int lu = u % UP;
+            const int oh = u / UP;
+            const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
+            float wr = fmaf(dp.x, qr[lu], dp.y * zr[lu]);
+            float wi = fmaf(dp.x, qi[lu], dp.y * zi[lu]);
+            wr = fminf(fmaxf(wr, -are), are);
+            wi = fminf(fmaxf(wi, -aim), aim);
+            const float dr0 = wr - zr[lu];
+            const float di0 = wi - zi[lu];
+            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+            const int owner = (lane & ~1) | oh;
+            const float dr = __shfl_sync(kFullMask, dr0, owner);
+            const float di = __shfl_sync(kFullMask, di0, owner);
+            const float4* gu = reinterpret_cast<const float4*>(sg + 2 * (u * NU + hf * UP));
+#pragma unroll
+            for (int l2 = 0; l2 < UP / 2; ++l2) {
+              const float4 g2 = gu[l2];
+              const int l = 2 * l2;
+              qr[l] = fmaf(-g2.x, dr, fmaf(-g2.y, di, qr[l]));
+              qi[l] = fmaf(-g2.x, di, fmaf(g2.y, dr, qi[l]));
+              qr[l + 1] = fmaf(-g2.z, dr, fmaf(-g2.w, di, qr[l + 1]));
+              qi[l + 1] = fmaf(-g2.z, di, fmaf(g2.w, dr, qi[l + 1]));
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (act) {
+#pragma unroll
+        for (int l = 0; l < UP; ++l) {
+          const int j = hf * UP + l;
+          sq[2 * (ts * NU + j)] = zr[l];
+          sq[2 * (ts * NU + j) + 1] = zi[l];
+        }
+      }
+      __syncwarp();
+    }
+    for (int f = lane; f < np * U; f += 32) {
+      const int ts = f / U;
+      const int u = f - ts * U;
+      const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
+      const long long o = (sc * T + tb + ts) * U + u;
+      if (P.xhat) P.xhat[o] = z;
+      if (P.llr) {
+        float* out = P.llr + o * P.Q;
+        const float inv = spre[4 * u + 3];
+        if (!(inv > 0.0f)) {
+          for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
+        } else {
+          const float rho = spre[4 * u + 2] * P.rho_scale;
+          dimension_llr(z.x * inv, rho, P, out);
+          if (!P.bpsk) dimension_llr(z.y * inv, rho, P, out + P.nb);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// Single problem: warp (= CTA) b takes subcarriers b, b + gridDim.x, ...
+__global__ void __launch_bounds__(32)
+ocd_projected_wide_kernel(const __grid_constant__ DetectParams P,
+                          const __grid_constant__ CUtensorMap ymap) {
+  using S = WideShape;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  unsigned char* ws = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const uint32_t bar0 = smem_addr(ws + S::kOffBar);
+  const long long gw = blockIdx.x;
+  if (gw >= P.Nsc) return;
+  if (lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ymap)) : "memory");
+    for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  wide_walk(P, &ymap, ws, bar0, parity, gw, P.Nsc, gridDim.x);
+}
+
+// Several problems: each warp draws tickets (runs of subcarriers of one
+// cell) from a device counter, as ocd_batched_tma_kernel.
+__global__ void __launch_bounds__(32)
+ocd_batched_wide_kernel(const __grid_constant__ BatchTable tab, unsigned int* __restrict__ tickets) {
+  using S = WideShape;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  unsigned char* ws = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const uint32_t bar0 = smem_addr(ws + S::kOffBar);
+  if (lane == 0) {
+    for (int i = 0; i < S::kStages; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  int c = 0, prefetched = -1;
+  for (;;) {
+    unsigned int tk = 0;
+    if (lane == 0) tk = atomicAdd(tickets, 1u);
+    tk = __shfl_sync(kFullMask, tk, 0);
+    if (tk >= tab.total) return;
+    while (tk >= tab.cell[c].tick_end) ++c;
+    const BatchCell& C = tab.cell[c];
+    if (c != prefetched) {
+      if (reinterpret_cast<uintptr_t>(&C.ymap) & 63u) {
+        if (lane == 0) atomicOr(&g_wide_fault, 2u);
+        return;
+      }
+      if (lane == 0)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&C.ymap)) : "memory");
+      prefetched = c;
+    }
+    const long long t0 = c ? tab.cell[c - 1].tick_end : 0;
+    const long long lo = ((long long)tk - t0) * C.sc_per_tick;
+    const long long hi = min(lo + (long long)C.sc_per_tick, (long long)C.P.Nsc);
+    if (!wide_walk(C.P, &C.ymap, ws, bar0, parity, lo, hi, 1)) return;
+  }
+}
+
+}  // namespace ocd

@@ -21,8 +21,8 @@ ALGOS = ["residual", "projected"]
 
 def algos_for(U, B=None):
     """Arrangements supporting the shape: projected for U <= 8, and for
-    U <= 16 when B is even (the bulk-copy kernel; test arrays are aligned)."""
-    if U <= 8 or (U <= 16 and B is not None and B % 2 == 0):
+    U <= 32 when B is even (the bulk-copy kernels; test arrays are aligned)."""
+    if U <= 8 or (U <= 32 and B is not None and B % 2 == 0):
         return ALGOS
     return ["residual"]
 
@@ -198,9 +198,9 @@ def test_full_size_sampled_against_oracle(algo):
     assert np.all(np.isfinite(L))
 
 
-@pytest.mark.parametrize("B,U", [(33, 9), (32, 17), (31, 16)])
+@pytest.mark.parametrize("B,U", [(33, 9), (33, 17), (31, 16), (35, 32)])
 def test_projected_rejects_unsupported_shapes(B, U):
-    """More than 16 users, or more than 8 with odd B (no bulk-copy staging)."""
+    """More than 8 users with odd B (no bulk-copy staging)."""
     d = synth.make_uplink(2, B, U, 2, 16, 10.0, 71)
     with pytest.raises(ocd.OcdError, match="UNSUPPORTED"):
         run_gpu(d, 3, orc.MMSE, 16, algo="projected")
@@ -221,4 +221,20 @@ def test_projected_symbol_passes_and_user_bounds(U, T):
     """Symbol counts around the per-pass width (16 symbols for U <= 8, 32 for
     U <= 4) and user counts around both instance bounds."""
     check(5, 40, U, T, 3, orc.BOX, 16, 8.0, 100 * U + T, label=f"U{U} T{T}",
+          algos=["projected"])
+
+
+@pytest.mark.parametrize("U", [17, 20, 24, 31, 32])
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_projected_four_user_tiles(mode, U):
+    """17..32 users (four 8-user tiles, G phase then q0 passes) in float32
+    storage: ragged last antenna block, several symbol passes."""
+    check(5, 100, U, 20, 4, mode, 64, 18.0, 600 + U, label=f"100x{U}", algos=["projected"])
+
+
+@pytest.mark.parametrize("B,U,T", [(256, 32, 14), (256, 32, 1), (512, 32, 2), (34, 18, 17),
+                                   (64, 32, 16), (2, 17, 3)])
+def test_projected_wide_shapes(B, U, T):
+    """The 256x32 cells of the batched workload, B = 512, tiny B, T = 1."""
+    check(4, B, U, T, 3, orc.BOX, 16, 15.0, B + U + T, label=f"{B}x{U} T{T}",
           algos=["projected"])
