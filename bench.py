@@ -228,6 +228,21 @@ def workload_config(args, nsc):
             "l2": "inputs larger than L2 (no flush)", "parallelism": f"subcarriers x{args.gpus}"}
 
 
+def form_summary(measure, args, keys):
+    """One of the extra forms measured beside the headline number, reduced to
+    `keys`; a failure is reported in the object instead of losing the line."""
+    import argparse as _ap
+    sub = _ap.Namespace(**vars(args))
+    sub.steps = min(args.steps, 50)
+    try:
+        res = measure(sub)
+    except Exception as exc:  # reported, not hidden: the key says what failed
+        return {"error": f"{type(exc).__name__}: {exc}"}
+    out = {k: res[k] for k in keys if k in res}
+    out["metric"] = res["metric"]
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -421,6 +436,11 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        if not args.no_forms:
+            line["batched_form"] = form_summary(measure_batched, args, (
+                "value", "unit", "ms_per_step", "arms_gbps", "roofline", "config"))
+            line["unfolded_form"] = form_summary(measure_unfolded, args, (
+                "value", "unit", "ms_per_step", "forward_ms", "roofline", "config"))
         if not args.no_cpu_baseline:
             r, el, done = cpu_oracle_rate(NSC_FRAME // 4, 99, args.cpu_seconds, args.mode)
             line["cpu_baseline"] = {
@@ -517,7 +537,7 @@ def batched_bound_s(spec, hbm_gbs, fma_tflops, projected):
     return max(t_hbm, t_alu), nbytes
 
 
-def run_batched(args):
+def measure_batched(args):
     """Mixed cells in one call: (B, U) in {(32,4), (64,8), (128,16), (256,32)},
     T in {1, 7, 14}, Nsc uniform in [300, 3300], K in [2, 5], MMSE / BOX,
     16 / 64-QAM (seeded).  Arms: the plain form (one ocd_detect per cell on one
@@ -598,11 +618,15 @@ def run_batched(args):
         "tune": tune.entries, "tune_seconds": tune_s,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_batched(args):
+    print(json.dumps(measure_batched(args)), flush=True)
     return 0
 
 
-def run_unfolded(args):
+def measure_unfolded(args):
     """Differentiable unfolded OCD-BOX: 128x16, K = 5, 4096 (subcarrier,
     symbol) samples (each its own channel), 16-QAM, SNR uniform in 5-25 dB per
     sample, BCE loss on the LLRs.  A step is forward + loss + adjoint."""
@@ -627,17 +651,17 @@ def run_unfolded(args):
     om = torch.full((k,), 0.9, device=dev, requires_grad=True)
     al = torch.full((k,), 0.05, device=dev, requires_grad=True)
 
-    def step():
+    def step(arr="projected"):
         om.grad = None
         al.grad = None
-        _, llr = ocd.unfolded_ocd(om, al, H, Yd, N0, 1.0, "box", order)
+        _, llr = ocd.unfolded_ocd(om, al, H, Yd, N0, 1.0, "box", order, algo=arr)
         loss = F.binary_cross_entropy_with_logits(llr, bits)
         loss.backward()
         return loss
 
-    def fwd():
+    def fwd(arr="projected"):
         with torch.no_grad():
-            ocd.unfolded_ocd(om, al, H, Yd, N0, 1.0, "box", order)
+            ocd.unfolded_ocd(om, al, H, Yd, N0, 1.0, "box", order, algo=arr)
 
     def timed(fn, steps):
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -654,17 +678,33 @@ def run_unfolded(args):
 
     steps = max(3, min(args.steps, 200))
     ms_fwd = timed(fwd, steps)
+    ms_res = timed(lambda: step("residual"), steps)
+    ms_eager = timed(step, steps)
+    # The same training step captured once in a CUDA graph (forward, loss,
+    # adjoint and the gradient reduction), replayed: device time without the
+    # host's per-step Python and launch overhead.
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        g_loss = step()
     sampler = ClockSampler(dev.index)
     with sampler:
-        ms = timed(step, steps)
+        ms = timed(graph.replay, steps)
     q = 4
     samples = nsc
-    # algorithmic work of one step: forward 8BUK + 2BU FMA, adjoint (replay +
-    # reverse) 16BUK + 2BU FMA per sample; bytes: H read twice, Y read, the
-    # checkpoints written and read, xhat / LLR written and read back
-    fma = samples * (24 * b * u * k + 4 * b * u)
-    nbytes = samples * (2 * 8 * b * u + 8 * b + 2 * k * (b + u) * 8 + 2 * (8 * u + 4 * u * q)
-                        + 4 * u * q)
+    # Algorithmic work of one step in the projected arrangement, per sample:
+    # G (upper triangle) 2BU(U+1) and q0 4BU FMA, sweeps 4U per update in the
+    # forward, the replay and the reverse (12KU^2); bytes: H and Y read once,
+    # G and the (q, z) checkpoints written and read, xhat / LLR written and
+    # read back, the LLR adjoint read.
+    fma = samples * (2 * b * u * (u + 1) + 4 * b * u + 12 * k * u * u)
+    nbytes = samples * (8 * b * u + 8 * b + 2 * 8 * u * u + 2 * k * 2 * u * 8
+                        + 2 * (8 * u + 4 * u * q) + 4 * u * q)
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -674,18 +714,26 @@ def run_unfolded(args):
         "metric": "training samples/s, unfolded OCD-BOX forward + adjoint (128x16, K=5, 16-QAM)",
         "workload": "unfolded", "value": samples / (ms / 1e3), "unit": "samples/s", "n_gpus": 1,
         "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "forward_ms": ms_fwd,
+        "arrangement": "projected (q = H^H r, G per sample)",
+        "timing": "CUDA-graph replay of the whole step (forward, BCE, adjoint, reduction)",
+        "eager_ms_per_step": ms_eager,
+        "residual_arrangement_eager_ms_per_step": ms_res,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic (i.i.d. Rayleigh H, "
         "Gray 16-QAM, AWGN at SNR uniform 5-25 dB per sample)",
         "config": {"workload": f"{samples} samples of 128x16, K=5, T=1, BCE loss", "B": b, "U": u,
-                   "K": k, "qam": order, "l2": "inputs 67 MB + checkpoints 24 MB (no flush)"},
+                   "K": k, "qam": order, "l2": "inputs 67 MB + checkpoints 13 MB (no flush)"},
         "roofline": {"bound": "max(hbm, fp32)", "bound_ms": t_bound * 1e3,
                      "frac": t_bound * 1e3 / ms, "achieved_tflops": 2.0 * fma / (ms / 1e3) / 1e12,
                      "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_peak": hbm,
                      "fp32_peak_tflops": fma_tf, "peak_source": f"{src} hbm_gbs; FP32 nominal"},
-        "loss": float(step()),
+        "loss": float(g_loss.detach()),
         "clocks": sampler.summary(),
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_unfolded(args):
+    print(json.dumps(measure_unfolded(args)), flush=True)
     return 0
 
 
@@ -701,6 +749,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and unfolded forms in the headline line")
     ap.add_argument("--workload", choices=["metric", "precision", "batched", "unfolded"], default="metric",
                     help="metric: the headline 128x8 configuration; precision: 256x16 K=4 in "
                          "float32 / bfloat16 / float16 storage with per-SNR accuracy; batched: "

@@ -281,9 +281,23 @@ int ocd_graph_destroy(ocd_graph_t* graph);
  * minimizing level.  H and Y are complex64 only.
  * ------------------------------------------------------------------------- */
 
-/* Device bytes of the per-sweep checkpoints (r and z at the start of each
- * sweep, complex64 [K][Nsc*T][B+U]). */
-size_t ocd_unfolded_checkpoint_size(int Nsc, int B, int U, int T, int K);
+/*
+ * Arrangements (`algo`, ocd_algo_t), identical in exact arithmetic:
+ *   OCD_ALGO_RESIDUAL   the residual r is carried (B entries per sample);
+ *                       checkpoints: r and z at the start of every sweep,
+ *                       complex64 [K][Nsc*T][B+U].
+ *   OCD_ALGO_PROJECTED  q = H^H r is carried (U entries) with G = H^H H per
+ *                       sample; checkpoints: G [Nsc*T][U][U], then q and z at
+ *                       the start of every sweep [K][Nsc*T][2U].  Needs the
+ *                       per-warp shared-memory copy of H to fit (every shape
+ *                       but the largest B with large U); OCD_ERR_UNSUPPORTED
+ *                       otherwise.
+ *   OCD_ALGO_AUTO       PROJECTED when it fits, else RESIDUAL.
+ * The forward and backward calls of one step must pass the same algo.
+ */
+
+/* Device bytes of the checkpoints of `algo` (layouts above). */
+size_t ocd_unfolded_checkpoint_size(int Nsc, int B, int U, int T, int K, int algo);
 /* Device workspace bytes of ocd_unfolded_backward (per-sample partial
  * gradients; a multiple of 256). */
 size_t ocd_unfolded_workspace_size(int Nsc, int T, int K);
@@ -296,20 +310,20 @@ size_t ocd_unfolded_workspace_size(int Nsc, int T, int K);
  *   K           1..OCD_MAX_SWEEPS; omega, alpha: device float [K].
  *   xhat        device complex64 [Nsc][T][U] (required: the adjoint reads it).
  *   llr         device float [Nsc][T][U][Q] or NULL.
- *   ckpt        device buffer of ocd_unfolded_checkpoint_size(...) bytes,
- *               written here and read by ocd_unfolded_backward.
+ *   ckpt        device buffer of ocd_unfolded_checkpoint_size(..., algo)
+ *               bytes, written here and read by ocd_unfolded_backward.
  */
 int ocd_unfolded_forward(const void* H, const void* Y, int Nsc, int B, int U, int T,
                          const float* N0, float Es, int K, int mode, int qam_order,
                          const float* omega, const float* alpha, void* xhat, float* llr,
-                         void* ckpt, cudaStream_t stream);
+                         void* ckpt, int algo, cudaStream_t stream);
 
 /*
  * ocd_unfolded_backward -- gradients of a loss with respect to omega and
  * alpha, given its gradients with respect to xhat (dxhat, complex64
  * [Nsc][T][U], adjoint convention dl/dRe + i dl/dIm) and to the LLRs (dllr,
  * float [Nsc][T][U][Q]); either may be NULL.  H, N0, omega, alpha, xhat and
- * ckpt are those of the forward call (unchanged since).  Writes domega and
+ * ckpt are those of the forward call (unchanged since; same algo).  Writes domega and
  * dalpha (device float [K]; summed over all samples in a fixed order, so the
  * result is deterministic).  workspace: ocd_unfolded_workspace_size(Nsc, T,
  * K) device bytes, 4-byte aligned.
@@ -318,7 +332,7 @@ int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const flo
                           float Es, int K, int mode, int qam_order, const float* omega,
                           const float* alpha, const void* xhat, const void* ckpt,
                           const void* dxhat, const float* dllr, float* domega, float* dalpha,
-                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
+                          void* workspace, size_t workspace_bytes, int algo, cudaStream_t stream);
 
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* ocd_last_error(void);

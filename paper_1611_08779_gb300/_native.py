@@ -75,12 +75,12 @@ SIGNATURES = {
     "ocd_graph_create_batched": (_i, [_vp, _i, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
     "ocd_graph_launch": (_i, [_vp, _vp]),
     "ocd_graph_destroy": (_i, [_vp]),
-    "ocd_unfolded_checkpoint_size": (_sz, [_i, _i, _i, _i, _i]),
+    "ocd_unfolded_checkpoint_size": (_sz, [_i, _i, _i, _i, _i, _i]),
     "ocd_unfolded_workspace_size": (_sz, [_i, _i, _i]),
     "ocd_unfolded_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _f, _i, _i, _i, _vp, _vp, _vp,
-                                  _vp, _vp, _vp]),
+                                  _vp, _vp, _i, _vp]),
     "ocd_unfolded_backward": (_i, [_vp, _i, _i, _i, _i, _vp, _f, _i, _i, _i, _vp, _vp, _vp, _vp,
-                                   _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+                                   _vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
     "ocd_fault_status": (_i, [_i]),
     "ocd_wait_selftest": (_i, [_i, _vp]),
     "ocd_last_error": (ctypes.c_char_p, []),

@@ -324,11 +324,14 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
       const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
       const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
       for (int k = 0; k < P.K; ++k) {
+        // users in two halves of UP (the owner half oh is a loop variable,
+        // the slot lu a compile-time index): half the code of a full unroll
+#pragma unroll 1
+        for (int oh = 0; oh < 2; ++oh) {
 #pragma unroll
-        for (int u = 0; u < NU; ++u) {
+        for (int lu = 0; lu < UP; ++lu) {
+          const int u = oh * UP + lu;
           if (u < U) {
-            const int lu = u % UP;
-            const int oh = u / UP;
             const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
             float wr = fmaf(dp.x, qr[lu], dp.y * zr[lu]);
             float wi = fmaf(dp.x, qi[lu], dp.y * zi[lu]);
@@ -351,6 +354,7 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
               qi[l + 1] = fmaf(-g2.z, di, fmaf(g2.w, dr, qi[l + 1]));
             }
           }
+        }
         }
       }
       __syncwarp();

@@ -32,7 +32,12 @@
 // shared load instead of a strided global one.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "ocd_common.cuh"
+#include "ocd_mma.cuh"
 #include "ocd_unfolded.h"
 
 namespace ocd {
@@ -380,6 +385,312 @@ ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Projected arrangement of the same unfolded sweeps (as for detection:
+// q = H^H r, q <- q - G[:, u] dz with G = H^H H, identical iterates in exact
+// arithmetic).  Lane j (< U) holds q_j, z_j, ||h_j||^2 and their adjoints; a
+// user update is one shuffle of dz from lane u and one complex FMA per lane
+// with column u of G from shared memory.  The checkpoints are G per sample
+// and (q, z) at the start of every sweep.
+// ---------------------------------------------------------------------------
+
+// Shared-memory words of one warp: channel copy (U + U%2 rows; the extra row
+// stays zero), received vector, G with row stride U + 1.
+template <int NA>
+__host__ __device__ inline int proj_warp_elems(int U) {
+  return (U + (U & 1)) * staged_stride<NA>() + 32 * NA + U * (U + 1);
+}
+
+// Checkpoint offsets (complex elements): G of sample s, then (q, z) of
+// sweep k for sample s.
+__host__ __device__ inline long long ckpt_g(const UnfoldParams& P, long long s) {
+  return s * P.U * P.U;
+}
+__host__ __device__ inline long long ckpt_qz(const UnfoldParams& P, int k, long long s) {
+  return P.samples * P.U * P.U + ((long long)k * P.samples + s) * 2 * P.U;
+}
+
+// One sweep in q-space.  KEEP: lane u records z_u before its update (zb) and
+// q_u at that time (qs).
+template <bool KEEP>
+__device__ __forceinline__ void qsweep(const UnfoldParams& P, const float2* sG, int gst, int lane,
+                                       float2& q, float2& z, float d, float p, float om,
+                                       float2& zb, float2& qs) {
+  for (int u = 0; u < P.U; ++u) {
+    float wr = fmaf(d, q.x, p * z.x);
+    float wi = fmaf(d, q.y, p * z.y);
+    project(wr, wi, P.D);
+    const float2 dz = shfl2(make_float2(om * (wr - z.x), om * (wi - z.y)), u);
+    if (lane == u) {
+      if (KEEP) {
+        zb = z;
+        qs = q;
+      }
+      z = make_float2(z.x + dz.x, z.y + dz.y);
+    }
+    const float2 g = lane < P.U ? sG[lane * gst + u] : make_float2(0.0f, 0.0f);
+    q.x = fmaf(-g.x, dz.x, fmaf(g.y, dz.y, q.x));
+    q.y = fmaf(-g.x, dz.y, fmaf(-g.y, dz.x, q.y));
+  }
+}
+
+// G = H^H H (Hermitian, diagonal real) into sG (row stride U + 1) and
+// q0 = H^H y into sy[0 .. U) (over y), from the user-major channel copy sH,
+// as realified m16n8k8 TF32 MMAs with the two-part split (hi*hi, hi*lo +
+// lo*hi; FP32-level accuracy).  A k-step covers antennas 4s + t (lane t of a
+// quad): A = [Re H^H; Im H^H] of user tile m, B = the same entries of user
+// tile n (G) or the received vector in column 0 (q0).  UT = user tiles.
+template <int UT, int NA>
+__device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float2* sG, int U,
+                                             int B, int lane) {
+  constexpr int st = staged_stride<NA>();
+  constexpr int NG = UT * (UT + 1) / 2;
+  const int gq = lane >> 2, t = lane & 3;
+  const int gst = U + 1;
+  float g[NG][2][4], qa[UT][2][4];
+#pragma unroll
+  for (int i = 0; i < NG; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { g[i][0][e] = 0.0f; g[i][1][e] = 0.0f; }
+#pragma unroll
+  for (int i = 0; i < UT; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { qa[i][0][e] = 0.0f; qa[i][1][e] = 0.0f; }
+  const int nks = (B + 3) / 4;
+  for (int ks = 0; ks < nks; ++ks) {
+    const int a = 4 * ks + t;  // < 32 NA: padding antennas hold zeros
+    uint32_t ah[UT][3], al[UT][3];
+#pragma unroll
+    for (int m = 0; m < UT; ++m) {
+      const int u = m * 8 + gq;
+      const float2 h = u < U ? sH[u * st + a] : make_float2(0.0f, 0.0f);
+      split_tf32(h.x, ah[m][0], al[m][0]);
+      split_tf32(h.y, ah[m][2], al[m][2]);
+      ah[m][1] = ah[m][2] ^ 0x80000000u;
+      al[m][1] = al[m][2] ^ 0x80000000u;
+    }
+    const float2 y = gq == 0 ? sy[a] : make_float2(0.0f, 0.0f);
+    uint32_t yh0, yl0, yh1, yl1;
+    split_tf32(y.x, yh0, yl0);
+    split_tf32(y.y, yh1, yl1);
+    int tile = 0;
+#pragma unroll
+    for (int m = 0; m < UT; ++m) {
+#pragma unroll
+      for (int n = m; n < UT; ++n, ++tile) {
+        mma_tf32(g[tile][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
+        mma_tf32(g[tile][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
+        mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
+      }
+      mma_tf32(qa[m][0], ah[m][0], ah[m][1], ah[m][2], yh0, yh1);
+      mma_tf32(qa[m][1], ah[m][0], ah[m][1], ah[m][2], yl0, yl1);
+      mma_tf32(qa[m][1], al[m][0], al[m][1], al[m][2], yh0, yh1);
+    }
+  }
+  __syncwarp();  // every lane's reads of sy are done before q0 overwrites it
+  int tile = 0;
+#pragma unroll
+  for (int m = 0; m < UT; ++m) {
+#pragma unroll
+    for (int n = m; n < UT; ++n, ++tile) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
+        if (i < U && j < U) {
+          float re = g[tile][1][e] + g[tile][0][e];
+          float im = g[tile][1][2 + e] + g[tile][0][2 + e];
+          if (i == j) im = 0.0f;  // G_uu is real
+          sG[i * gst + j] = make_float2(re, im);
+          if (n != m) sG[j * gst + i] = make_float2(re, -im);
+        }
+      }
+    }
+    const int u = m * 8 + gq;
+    if (t == 0 && u < U)  // column 0 holds q0: rows gq (re) and gq + 8 (im)
+      sy[u] = make_float2(qa[m][1][0] + qa[m][0][0], qa[m][1][2] + qa[m][0][2]);
+  }
+}
+
+template <int NA>
+__global__ void __launch_bounds__(128)
+ocd_unfolded_proj_forward_kernel(const __grid_constant__ UnfoldParams P) {
+  extern __shared__ float2 unf_smem[];
+  constexpr int st = staged_stride<NA>();
+  const int lane = threadIdx.x & 31;
+  const int U = P.U, B = P.B;
+  const int rows = U + (U & 1);
+  const int gst = U + 1;
+  float2* sH = unf_smem + (threadIdx.x >> 5) * proj_warp_elems<NA>(U);
+  float2* sy = sH + rows * st;
+  float2* sG = sy + 32 * NA;
+  for (int i = lane; i < rows * st + 32 * NA; i += 32) sH[i] = make_float2(0.0f, 0.0f);
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.samples;
+       s += nw) {
+    const long long w = s / P.T;
+    Warp<NA, true> W{P, P.H + w * B * U, sH, lane};
+    W.stage();  // ends with __syncwarp
+    for (int b = lane; b < B; b += 32) sy[b] = __ldg(P.Y + s * B + b);
+    __syncwarp();
+    // G = H^H H and q0 = H^H y on the tensor cores
+    if (U <= 8) gram_q0_tf32<1, NA>(sH, sy, sG, U, B, lane);
+    else if (U <= 16) gram_q0_tf32<2, NA>(sH, sy, sG, U, B, lane);
+    else gram_q0_tf32<4, NA>(sH, sy, sG, U, B, lane);
+    __syncwarp();
+    float2 q = lane < U ? sy[lane] : make_float2(0.0f, 0.0f);  // q0 (written over y)
+    const float nrm = lane < U ? sG[lane * gst + lane].x : 0.0f;
+    float2* ckG = P.ckpt + ckpt_g(P, s);
+    for (int e = lane; e < U * U; e += 32) ckG[e] = sG[(e / U) * gst + (e % U)];
+    float2 z = make_float2(0.0f, 0.0f), zb = z, qs = z;
+    for (int k = 0; k < P.K; ++k) {
+      if (lane < U) {
+        float2* ck = P.ckpt + ckpt_qz(P, k, s);
+        ck[lane] = q;
+        ck[U + lane] = z;
+      }
+      float d, p;
+      gains(nrm, __ldg(P.alpha + k), d, p);
+      qsweep<false>(P, sG, gst, lane, q, z, d, p, __ldg(P.omega + k), zb, qs);
+    }
+    if (lane < U) {
+      const long long o = s * U + lane;
+      P.xhat[o] = z;
+      if (P.llr) {
+        float d, p;
+        gains(nrm, __ldg(P.alpha + P.K - 1), d, p);
+        DetectParams D = P.D;
+        D.rho_scale = P.es / __ldg(P.N0 + w);
+        user_llr(z, nrm, p, D, P.llr + o * P.D.Q);
+      }
+    }
+    __syncwarp();  // sG and sy are rewritten by the next sample
+  }
+}
+
+__global__ void __launch_bounds__(128)
+ocd_unfolded_proj_backward_kernel(const __grid_constant__ UnfoldParams P) {
+  extern __shared__ float2 unf_smem[];
+  const int lane = threadIdx.x & 31;
+  const int U = P.U;
+  const int gst = U + 1;
+  const int K = P.K;
+  float2* sG = unf_smem + (threadIdx.x >> 5) * U * gst;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.samples;
+       s += nw) {
+    const long long w = s / P.T;
+    __syncwarp();
+    const float2* ckG = P.ckpt + ckpt_g(P, s);
+    for (int e = lane; e < U * U; e += 32) sG[(e / U) * gst + (e % U)] = ckG[e];
+    __syncwarp();
+    const float nrm = lane < U ? sG[lane * gst + lane].x : 0.0f;
+    // ---- adjoint of the soft output and of xhat (lane u)
+    float2 zbar = make_float2(0.0f, 0.0f);
+    float al_mu = 0.0f;
+    if (lane < U) {
+      const long long o = s * U + lane;
+      if (P.dxhat) zbar = __ldg(P.dxhat + o);
+      if (P.dllr) {
+        float d, p;
+        gains(nrm, __ldg(P.alpha + K - 1), d, p);
+        if (p > 0.0f) {
+          const float2 z = __ldg(P.xhat + o);
+          const float rho = nrm * P.es / __ldg(P.N0 + w);
+          const float inv = 1.0f / (p * P.D.sqrt_es);
+          const float* g = P.dllr + o * P.D.Q;
+          const float xr = z.x * inv;
+          const float sr = dimension_llr_slope(xr, rho, P.D, g);
+          zbar.x += sr * inv;
+          float mubar = -sr * xr / p;
+          if (!P.D.bpsk) {
+            const float xi = z.y * inv;
+            const float si = dimension_llr_slope(xi, rho, P.D, g + P.D.nb);
+            zbar.y += si * inv;
+            mubar -= si * xi / p;
+          }
+          al_mu = mubar * (-p * d);
+        }
+      }
+    }
+    al_mu = warp_sum(al_mu);
+    float2 qbar = make_float2(0.0f, 0.0f);
+    float* part = P.partial + s * 2 * K;
+    for (int k = K - 1; k >= 0; --k) {
+      const float om = __ldg(P.omega + k);
+      float d, p;
+      gains(nrm, __ldg(P.alpha + k), d, p);
+      float2 q = make_float2(0.0f, 0.0f), z = q;
+      if (lane < U) {
+        const float2* ck = P.ckpt + ckpt_qz(P, k, s);
+        q = ck[lane];
+        z = ck[U + lane];
+      }
+      float2 zb = make_float2(0.0f, 0.0f), qs = zb;
+      qsweep<true>(P, sG, gst, lane, q, z, d, p, om, zb, qs);
+      float om_l = 0.0f, al_l = 0.0f;  // lane u accumulates the terms of user u
+      for (int u = U - 1; u >= 0; --u) {
+        const float2 g = lane < U ? sG[lane * gst + u] : make_float2(0.0f, 0.0f);
+        // G[:, u]^H q'  (conj(G[j][u]) q'_j summed over j)
+        float2 hr = make_float2(fmaf(g.x, qbar.x, g.y * qbar.y), fmaf(g.x, qbar.y, -g.y * qbar.x));
+        hr = warp_sum2(hr);
+        if (lane == u) {
+          const float wr0 = fmaf(d, qs.x, p * zb.x);
+          const float wi0 = fmaf(d, qs.y, p * zb.y);
+          float cr = wr0, ci = wi0;
+          project(cr, ci, P.D);
+          float mr = 1.0f, mi = 1.0f;
+          if (P.D.box) {
+            mr = fabsf(wr0) < P.D.box_a ? 1.0f : 0.0f;
+            mi = (!P.D.bpsk && fabsf(wi0) < P.D.box_a) ? 1.0f : 0.0f;
+          }
+          const float gr = zbar.x - hr.x, gi = zbar.y - hr.y;
+          om_l = fmaf(cr - zb.x, gr, fmaf(ci - zb.y, gi, om_l));
+          const float wbr = mr * om * gr, wbi = mi * om * gi;
+          zbar = make_float2(zbar.x - om * gr + p * wbr, zbar.y - om * gi + p * wbi);
+          qbar = make_float2(fmaf(d, wbr, qbar.x), fmaf(d, wbi, qbar.y));
+          al_l -= d * d * fmaf(qs.x, wbr, qs.y * wbi) + p * d * fmaf(zb.x, wbr, zb.y * wbi);
+        }
+      }
+      float om_bar = warp_sum(om_l);
+      float al_bar = warp_sum(al_l);
+      if (k == K - 1) al_bar += al_mu;
+      if (lane == 0) {
+        part[2 * k] = om_bar;
+        part[2 * k + 1] = al_bar;
+      }
+    }
+  }
+}
+
+// cudaFuncSetAttribute once per (device, kernel, size): the launches below
+// stay free of attribute calls (and capturable) after the first one.
+cudaError_t allow_smem(const void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{dev, fn}];
+  if (have >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) have = smem;
+  return e;
+}
+
+template <int NA>
+cudaError_t launch_proj(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
+  const size_t smem = backward ? 4ull * P.U * (P.U + 1) * sizeof(float2)
+                               : 4ull * proj_warp_elems<NA>(P.U) * sizeof(float2);
+  const void* fn = backward ? reinterpret_cast<const void*>(ocd_unfolded_proj_backward_kernel)
+                            : reinterpret_cast<const void*>(ocd_unfolded_proj_forward_kernel<NA>);
+  cudaError_t e = allow_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  if (backward) ocd_unfolded_proj_backward_kernel<<<grid, 128, smem, stream>>>(P);
+  else ocd_unfolded_proj_forward_kernel<NA><<<grid, 128, smem, stream>>>(P);
+  return cudaGetLastError();
+}
+
 constexpr size_t kUnfoldedSmemLimit = 192 * 1024;  // per CTA of 4 warps
 
 template <int NA>
@@ -388,7 +699,7 @@ cudaError_t launch_pair(const UnfoldParams& P, bool backward, unsigned grid, cud
   if (smem <= kUnfoldedSmemLimit) {
     const void* fn = backward ? reinterpret_cast<const void*>(ocd_unfolded_backward_kernel<NA, true>)
                               : reinterpret_cast<const void*>(ocd_unfolded_forward_kernel<NA, true>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     if (backward) ocd_unfolded_backward_kernel<NA, true><<<grid, 128, smem, stream>>>(P);
     else ocd_unfolded_forward_kernel<NA, true><<<grid, 128, smem, stream>>>(P);
@@ -401,6 +712,13 @@ cudaError_t launch_pair(const UnfoldParams& P, bool backward, unsigned grid, cud
 
 }  // namespace
 
+bool projected_fits(int B, int U) {
+  const int na = (B + 31) / 32;
+  const int n2 = na <= 1 ? 1 : na <= 2 ? 2 : na <= 4 ? 4 : na <= 8 ? 8 : 16;
+  const size_t words = (size_t)(U + (U & 1)) * (32 * n2 + 1) + 32 * n2 + (size_t)U * (U + 1);
+  return 4 * words * sizeof(float2) <= kUnfoldedSmemLimit;
+}
+
 cudaError_t launch_unfolded(const UnfoldParams& P, bool backward, int sms, cudaStream_t stream) {
   if (P.samples == 0) return cudaSuccess;
   long long grid = (P.samples + 3) / 4;
@@ -408,7 +726,13 @@ cudaError_t launch_unfolded(const UnfoldParams& P, bool backward, int sms, cudaS
   if (grid > cap) grid = cap;
   const int na = (P.B + 31) / 32;
   cudaError_t e;
-  if (na <= 1) e = launch_pair<1>(P, backward, (unsigned)grid, stream);
+  if (P.projected) {
+    if (na <= 1) e = launch_proj<1>(P, backward, (unsigned)grid, stream);
+    else if (na <= 2) e = launch_proj<2>(P, backward, (unsigned)grid, stream);
+    else if (na <= 4) e = launch_proj<4>(P, backward, (unsigned)grid, stream);
+    else if (na <= 8) e = launch_proj<8>(P, backward, (unsigned)grid, stream);
+    else e = launch_proj<16>(P, backward, (unsigned)grid, stream);
+  } else if (na <= 1) e = launch_pair<1>(P, backward, (unsigned)grid, stream);
   else if (na <= 2) e = launch_pair<2>(P, backward, (unsigned)grid, stream);
   else if (na <= 4) e = launch_pair<4>(P, backward, (unsigned)grid, stream);
   else if (na <= 8) e = launch_pair<8>(P, backward, (unsigned)grid, stream);
@@ -434,10 +758,19 @@ using namespace ocdh;
 
 namespace {
 
+// OCD_ALGO_AUTO takes the projected arrangement whenever its shared-memory
+// copy fits (every shape up to 512 x 32 except the largest B with large U).
+int resolve_unfolded_algo(int algo, int B, int U) {
+  if (algo == OCD_ALGO_AUTO) return ocd::projected_fits(B, U) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  return algo;
+}
+
 int unfolded_common(const void* H, int Nsc, int B, int U, int T, const float* N0, float Es,
                     int K, int mode, int qam_order, const float* omega, const float* alpha,
-                    const void* xhat, const void* ckpt, ocd::UnfoldParams& P) {
+                    const void* xhat, const void* ckpt, int algo, ocd::UnfoldParams& P) {
   Alphabet al;
+  if (algo != OCD_ALGO_AUTO && algo != OCD_ALGO_RESIDUAL && algo != OCD_ALGO_PROJECTED)
+    return fail(OCD_ERR_ARG, "unknown algo %d", algo);
   if (Nsc < 0 || T < 0) return fail(OCD_ERR_ARG, "Nsc=%d and T=%d must be >= 0", Nsc, T);
   if (B < 1 || B > OCD_MAX_ANTENNAS) return fail(OCD_ERR_ARG, "B=%d outside 1..%d", B, OCD_MAX_ANTENNAS);
   if (U < 1 || U > OCD_MAX_USERS) return fail(OCD_ERR_ARG, "U=%d outside 1..%d", U, OCD_MAX_USERS);
@@ -463,6 +796,10 @@ int unfolded_common(const void* H, int Nsc, int B, int U, int T, const float* N0
   P.samples = samples;
   P.Nsc = Nsc; P.B = B; P.U = U; P.T = T; P.K = K;
   P.es = Es;
+  algo = resolve_unfolded_algo(algo, B, U);
+  if (algo == OCD_ALGO_PROJECTED && !ocd::projected_fits(B, U))
+    return fail(OCD_ERR_UNSUPPORTED, "projected unfolded form: B=%d U=%d exceeds shared memory", B, U);
+  P.projected = algo == OCD_ALGO_PROJECTED;
   return OCD_OK;
 }
 
@@ -481,9 +818,12 @@ int sms_of_current(int& sms) {
 
 extern "C" {
 
-size_t ocd_unfolded_checkpoint_size(int Nsc, int B, int U, int T, int K) {
+size_t ocd_unfolded_checkpoint_size(int Nsc, int B, int U, int T, int K, int algo) {
   if (Nsc <= 0 || T <= 0 || B <= 0 || U <= 0 || K <= 0) return 0;
-  return (size_t)K * Nsc * T * (B + U) * sizeof(float2);
+  const size_t S = (size_t)Nsc * T;
+  if (resolve_unfolded_algo(algo, B, U) == OCD_ALGO_PROJECTED)
+    return (S * U * U + (size_t)K * S * 2 * U) * sizeof(float2);
+  return (size_t)K * S * (B + U) * sizeof(float2);
 }
 
 size_t ocd_unfolded_workspace_size(int Nsc, int T, int K) {
@@ -495,9 +835,10 @@ size_t ocd_unfolded_workspace_size(int Nsc, int T, int K) {
 int ocd_unfolded_forward(const void* H, const void* Y, int Nsc, int B, int U, int T,
                          const float* N0, float Es, int K, int mode, int qam_order,
                          const float* omega, const float* alpha, void* xhat, float* llr,
-                         void* ckpt, cudaStream_t stream) {
+                         void* ckpt, int algo, cudaStream_t stream) {
   ocd::UnfoldParams P;
-  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt, P);
+  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt,
+                           algo, P);
   if (st != OCD_OK) return st;
   if (P.samples > 0 && !Y) return fail(OCD_ERR_ARG, "Y must not be NULL");
   if (((uintptr_t)Y & 7u) || ((uintptr_t)llr & 3u))
@@ -517,9 +858,10 @@ int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const flo
                           float Es, int K, int mode, int qam_order, const float* omega,
                           const float* alpha, const void* xhat, const void* ckpt,
                           const void* dxhat, const float* dllr, float* domega, float* dalpha,
-                          void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+                          void* workspace, size_t workspace_bytes, int algo, cudaStream_t stream) {
   ocd::UnfoldParams P;
-  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt, P);
+  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt,
+                           algo, P);
   if (st != OCD_OK) return st;
   if (!domega || !dalpha) return fail(OCD_ERR_ARG, "domega and dalpha must not be NULL");
   if (((uintptr_t)dxhat & 7u) || (((uintptr_t)dllr | (uintptr_t)domega | (uintptr_t)dalpha |

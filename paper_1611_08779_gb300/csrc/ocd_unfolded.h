@@ -25,9 +25,12 @@ struct UnfoldParams {
   long long samples;                    // Nsc * T
   int Nsc, B, U, T, K;
   float es;
+  int projected;                        // 1: q-space arrangement (checkpoints G and (q, z))
 };
 
 // Forward (backward = false) or adjoint + reduction (backward = true).
 cudaError_t launch_unfolded(const UnfoldParams& P, bool backward, int sms, cudaStream_t stream);
+// Whether the projected arrangement's shared-memory copy fits for (B, U).
+bool projected_fits(int B, int U);
 
 }  // namespace ocd

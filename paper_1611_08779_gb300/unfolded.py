@@ -11,7 +11,7 @@ from __future__ import annotations
 import torch
 
 from . import _native
-from .api import _check_c64, _mode, _stream_handle, bits_per_symbol
+from .api import ALGOS, _check_c64, _mode, _stream_handle, bits_per_symbol
 
 
 def _f32(name, t, n, dev):
@@ -21,10 +21,10 @@ def _f32(name, t, n, dev):
 
 
 class UnfoldedOCD(torch.autograd.Function):
-    """(omega, alpha, H, Y, N0, Es, mode, qam_order) -> (xhat, llr)."""
+    """(omega, alpha, H, Y, N0, Es, mode, qam_order, algo) -> (xhat, llr)."""
 
     @staticmethod
-    def forward(ctx, omega, alpha, H, Y, N0, Es=1.0, mode="box", qam_order=16):
+    def forward(ctx, omega, alpha, H, Y, N0, Es=1.0, mode="box", qam_order=16, algo="auto"):
         lib = _native.load()
         _check_c64("H", H)
         _check_c64("Y", Y, H.device)
@@ -40,25 +40,29 @@ class UnfoldedOCD(torch.autograd.Function):
         _f32("alpha", alpha, K, dev)
         _f32("N0", N0, Nsc, dev)
         Q = bits_per_symbol(qam_order)
+        if algo not in ALGOS:
+            raise ValueError(f"unknown algo {algo!r}")
+        code = ALGOS[algo]
         xhat = torch.empty((Nsc, T, U), dtype=torch.complex64, device=dev)
         llr = torch.empty((Nsc, T, U, Q), dtype=torch.float32, device=dev)
-        nck = lib.ocd_unfolded_checkpoint_size(Nsc, B, U, T, K)
+        nck = lib.ocd_unfolded_checkpoint_size(Nsc, B, U, T, K, code)
         ckpt = torch.empty(max(int(nck), 8), dtype=torch.uint8, device=dev)
         with torch.cuda.device(dev):
             st = lib.ocd_unfolded_forward(H.data_ptr(), Y.data_ptr(), Nsc, B, U, T, N0.data_ptr(),
                                           float(Es), K, _mode(mode), int(qam_order),
                                           omega.data_ptr(), alpha.data_ptr(), xhat.data_ptr(),
-                                          llr.data_ptr(), ckpt.data_ptr(), _stream_handle(None))
+                                          llr.data_ptr(), ckpt.data_ptr(), code,
+                                          _stream_handle(None))
         _native.check(st)
         ctx.save_for_backward(omega, alpha, H, N0, xhat, ckpt)
-        ctx.args = (float(Es), _mode(mode), int(qam_order))
+        ctx.args = (float(Es), _mode(mode), int(qam_order), code)
         return xhat, llr
 
     @staticmethod
     def backward(ctx, gx, gl):
         lib = _native.load()
         omega, alpha, H, N0, xhat, ckpt = ctx.saved_tensors
-        Es, mode, order = ctx.args
+        Es, mode, order, code = ctx.args
         Nsc, B, U = H.shape
         T = xhat.shape[1]
         K = omega.numel()
@@ -76,12 +80,13 @@ class UnfoldedOCD(torch.autograd.Function):
                                            gx.data_ptr() if gx is not None else None,
                                            gl.data_ptr() if gl is not None else None,
                                            domega.data_ptr(), dalpha.data_ptr(), ws.data_ptr(),
-                                           ws.numel(), _stream_handle(None))
+                                           ws.numel(), code, _stream_handle(None))
         _native.check(st)
-        return domega, dalpha, None, None, None, None, None, None
+        return domega, dalpha, None, None, None, None, None, None, None
 
 
-def unfolded_ocd(omega, alpha, H, Y, N0, Es=1.0, mode="box", qam_order=16):
+def unfolded_ocd(omega, alpha, H, Y, N0, Es=1.0, mode="box", qam_order=16, algo="auto"):
     """Differentiable unfolded OCD: returns (xhat, llr); gradients reach
-    omega and alpha through the library's adjoint kernel."""
-    return UnfoldedOCD.apply(omega, alpha, H, Y, N0, Es, mode, qam_order)
+    omega and alpha through the library's adjoint kernel.  `algo`: "auto",
+    "residual" or "projected" (see include/ocd.h)."""
+    return UnfoldedOCD.apply(omega, alpha, H, Y, N0, Es, mode, qam_order, algo)

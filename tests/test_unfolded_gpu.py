@@ -54,24 +54,29 @@ def reference(H, Y, N0, om, al, mode, order, bits=None):
                                       al.astype(np.float64), MODE[mode], order, bits)
 
 
-def gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t):
+def gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t, arr="auto"):
     o = torch.tensor(om, device="cuda", requires_grad=True)
     a = torch.tensor(al, device="cuda", requires_grad=True)
-    x, llr = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, mode, order)
+    x, llr = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, mode, order, algo=arr)
     loss = torch.nn.functional.binary_cross_entropy_with_logits(llr, bits_t)
     loss.backward()
     return float(loss), o.grad.cpu().numpy(), a.grad.cpu().numpy()
 
 
+ARR = ["residual", "projected"]
+
+
+@pytest.mark.parametrize("arr", ARR)
 @pytest.mark.parametrize("mode", ["box", "mmse"])
 @pytest.mark.parametrize("B,U,T,K,order", [(128, 16, 2, 5, 16), (32, 8, 3, 3, 64), (33, 5, 4, 2, 4),
-                                           (64, 32, 1, 4, 16), (300, 7, 2, 3, 2), (512, 3, 1, 2, 256)])
-def test_forward_matches_the_fp64_reference(mode, B, U, T, K, order):
+                                           (64, 32, 1, 4, 16), (300, 7, 2, 3, 2), (512, 3, 1, 2, 256),
+                                           (96, 31, 2, 3, 16), (2, 1, 3, 2, 4)])
+def test_forward_matches_the_fp64_reference(mode, B, U, T, K, order, arr):
     H, Y, N0, _ = problem(12, B, U, T, order, seed=B + U + T + K)
     om, al = params(K, seed=K)
     Hd, Yd, N0d = to_dev(H, Y, N0)
     x, llr = ocd.unfolded_ocd(torch.tensor(om, device="cuda"), torch.tensor(al, device="cuda"),
-                              Hd, Yd, N0d, 1.0, mode, order)
+                              Hd, Yd, N0d, 1.0, mode, order, algo=arr)
     torch.cuda.synchronize()
     z_ref, l_ref = reference(H, Y, N0, om, al, mode, order)
     assert xhat_error(x.cpu().numpy(), z_ref) <= 1e-4
@@ -81,32 +86,35 @@ def test_forward_matches_the_fp64_reference(mode, B, U, T, K, order):
     assert hard_bit_mismatches(llr.cpu().numpy(), l_ref, z_ref, p, order) == 0
 
 
+@pytest.mark.parametrize("arr", ARR)
 @pytest.mark.parametrize("mode", ["box", "mmse"])
-@pytest.mark.parametrize("B,U,T,K,order", [(128, 16, 2, 5, 16), (48, 8, 4, 3, 64), (20, 3, 3, 2, 2)])
-def test_gradients_match_fp64_autograd(mode, B, U, T, K, order):
+@pytest.mark.parametrize("B,U,T,K,order", [(128, 16, 2, 5, 16), (48, 8, 4, 3, 64), (20, 3, 3, 2, 2),
+                                           (64, 32, 1, 3, 16)])
+def test_gradients_match_fp64_autograd(mode, B, U, T, K, order, arr):
     H, Y, N0, bits = problem(32, B, U, T, order, seed=7 * B + U)
     om, al = params(K, seed=U + K)
     loss_ref, gom_ref, gal_ref = reference(H, Y, N0, om, al, mode, order, bits)
     Hd, Yd, N0d = to_dev(H, Y, N0)
     bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
-    loss, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t)
+    loss, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t, arr)
     assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
     g = np.concatenate([gom, gal])
     g_ref = np.concatenate([gom_ref, gal_ref])
     assert np.linalg.norm(g - g_ref) <= 2e-3 * np.linalg.norm(g_ref) + 1e-6, (g, g_ref)
 
 
-def test_gradient_matches_finite_differences_of_the_gpu_forward():
+@pytest.mark.parametrize("arr", ARR)
+def test_gradient_matches_finite_differences_of_the_gpu_forward(arr):
     H, Y, N0, bits = problem(64, 64, 8, 2, 16, seed=31)
     om, al = params(4, seed=3)
     Hd, Yd, N0d = to_dev(H, Y, N0)
     bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
-    _, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    _, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, arr)
 
     def f(o, a):
         with torch.no_grad():
             _, llr = ocd.unfolded_ocd(torch.tensor(o, device="cuda"), torch.tensor(a, device="cuda"),
-                                      Hd, Yd, N0d, 1.0, "box", 16)
+                                      Hd, Yd, N0d, 1.0, "box", 16, algo=arr)
             return float(torch.nn.functional.binary_cross_entropy_with_logits(llr.double(), bits_t.double()))
 
     eps = 2e-3
@@ -139,14 +147,42 @@ def test_gradient_through_xhat_only():
     assert np.linalg.norm(g - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
 
 
-def test_backward_is_deterministic():
+@pytest.mark.parametrize("arr", ARR)
+def test_backward_is_deterministic(arr):
     H, Y, N0, bits = problem(256, 64, 8, 2, 16, seed=51)
     om, al = params(3, seed=6)
     Hd, Yd, N0d = to_dev(H, Y, N0)
     bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
-    r1 = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
-    r2 = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    r1 = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, arr)
+    r2 = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, arr)
     assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+
+
+def test_arrangements_agree():
+    """Residual and projected arrangements: same values and gradients up to
+    FP32 rounding (identical in exact arithmetic)."""
+    H, Y, N0, bits = problem(128, 128, 16, 1, 16, seed=52)
+    om, al = params(5, seed=8)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    res = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, "residual")
+    prj = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, "projected")
+    assert abs(res[0] - prj[0]) <= 1e-5 * abs(res[0])
+    g1 = np.concatenate(res[1:])
+    g2 = np.concatenate(prj[1:])
+    assert np.linalg.norm(g1 - g2) <= 2e-3 * np.linalg.norm(g1)
+
+
+def test_projected_rejects_a_channel_copy_that_does_not_fit():
+    H, Y, N0, _ = problem(2, 512, 32, 1, 16, seed=53)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    with pytest.raises(ocd.OcdError, match="UNSUPPORTED"):
+        ocd.unfolded_ocd(torch.ones(2, device="cuda"), torch.zeros(2, device="cuda"), Hd, Yd, N0d,
+                         1.0, "box", 16, algo="projected")
+    x, _ = ocd.unfolded_ocd(torch.ones(2, device="cuda"), torch.zeros(2, device="cuda"), Hd, Yd, N0d,
+                            1.0, "box", 16)  # auto -> residual arrangement
+    torch.cuda.synchronize()
+    assert torch.all(torch.isfinite(torch.view_as_real(x)))
 
 
 def test_undamped_forward_is_algorithm_1():
