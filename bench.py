@@ -457,11 +457,12 @@ def run_ours(args):
 def run_precision(args):
     """256x16, 3300 subcarriers, T = 14, K = 4, 64-QAM with H and Y stored as
     float32, bfloat16 and float16 pairs: throughput of each (inputs 198 MB in
-    float32 > L2), and per-SNR error against the FP64 oracle evaluated on the
-    unquantized inputs (sampled subcarriers)."""
+    float32 > L2), and per SNR the difference of the 16-bit forms from the
+    float32-storage result and the uncoded bit error rate against the sent
+    bits.  (The per-SNR error against the FP64 reference is measured by the
+    test-suite: tests/test_precision_gpu.py.)"""
     import torch
 
-    import oracle as orc
     import paper_1611_08779_gb300 as ocd
     from paper_1611_08779_gb300 import synth
     b, u, t, k, q, nsc = 256, 16, 14, 4, 6, 3300
@@ -490,28 +491,26 @@ def run_precision(args):
         nbytes = algorithmic_bytes_per_sc_stored(b, u, t, q, elem) * nsc
         out[name] = {"value": nsc * t * u * q / (ms / 1e3) / 1e9, "unit": "Gb/s",
                      "ms_per_step": ms, "hbm_frac": nbytes / (ms / 1e3) / 1e9 / peak}
-    # accuracy per SNR against the FP64 oracle on unquantized inputs
     per_snr = {}
-    m = orc.BOX if args.mode == "box" else orc.MMSE
     for snr in range(0, 31, 5):
-        ds = synth.make_uplink(48, b, u, t, ORDER, float(snr), seed=100 + snr, dtype=np.complex128)
-        z_ref, l_ref = orc.ocd_detect(ds["H"], ds["Y"], ds["N0"], 1.0, k, m, ORDER)
-        row = {}
-        for name, dt in (("f32", None), ("bf16", torch.bfloat16), ("f16", torch.float16)):
-            h = torch.from_numpy(ds["H"].astype(np.complex64)).to(dev)
-            y = torch.from_numpy(ds["Y"].astype(np.complex64)).to(dev)
-            if dt is not None:
-                h, y = to16(h, dt), to16(y, dt)
-            x, l = ocd.ocd_detect(h, y, ds["N0"], 1.0, k, args.mode, ORDER)
+        ds = synth.make_uplink(480, b, u, t, ORDER, float(snr), seed=100 + snr)
+        h32 = torch.from_numpy(ds["H"]).to(dev)
+        y32 = torch.from_numpy(ds["Y"]).to(dev)
+        x32, l32 = ocd.ocd_detect(h32, y32, ds["N0"], 1.0, k, args.mode, ORDER)
+        x32 = x32.cpu().numpy()
+        l32 = l32.cpu().numpy()
+        row = {"f32": {"ber_vs_sent": float(np.mean((l32 > 0).astype(np.uint8) != ds["bits"]))}}
+        for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+            x, l = ocd.ocd_detect(to16(h32, dt), to16(y32, dt), ds["N0"], 1.0, k, args.mode, ORDER)
             x = x.cpu().numpy()
             l = l.cpu().numpy()
-            xe = np.max(np.linalg.norm(x - z_ref, axis=-1)
-                        / np.maximum(np.linalg.norm(z_ref, axis=-1), 1e-3 * math.sqrt(u)))
-            le = np.abs(l - l_ref) / np.maximum(np.abs(l_ref), 1.0)
-            row[name] = {"xhat_rel_err_max": float(xe), "llr_rel_err_p99": float(np.quantile(le, 0.99)),
-                         "hard_bit_mismatch_vs_oracle": float(np.mean((l > 0) != (l_ref > 0))),
+            xe = np.max(np.linalg.norm(x - x32, axis=-1)
+                        / np.maximum(np.linalg.norm(x32, axis=-1), 1e-3 * math.sqrt(u)))
+            le = np.abs(l - l32) / np.maximum(np.abs(l32), 1.0)
+            row[name] = {"xhat_rel_diff_vs_f32_max": float(xe),
+                         "llr_rel_diff_vs_f32_p99": float(np.quantile(le, 0.99)),
+                         "hard_bit_mismatch_vs_f32": float(np.mean((l > 0) != (l32 > 0))),
                          "ber_vs_sent": float(np.mean((l > 0).astype(np.uint8) != ds["bits"]))}
-        row["oracle_ber_vs_sent"] = float(np.mean((l_ref > 0).astype(np.uint8) != ds["bits"]))
         per_snr[str(snr)] = row
     line = {"metric": "detected Gb/s, precision form (256x16, 64-QAM, K=4, T=14)",
             "workload": "precision", "unit": "Gb/s", "n_gpus": 1, "steps": args.steps,
@@ -519,9 +518,11 @@ def run_precision(args):
             "config": {"workload": f"OCD-{args.mode.upper()} 256x16 64-QAM K=4 T=14, "
                                    f"{nsc} subcarriers per step", "B": b, "U": u, "T": t, "K": k},
             "forms": out, "accuracy_per_snr_db": per_snr,
-            "accuracy_sample": "48 subcarriers x 14 symbols per SNR, FP64 oracle on unquantized inputs"}
+            "accuracy_sample": "480 subcarriers x 14 symbols per SNR; 16-bit forms against the "
+                               "float32-storage result, and uncoded BER against the sent bits"}
     print(json.dumps(line), flush=True)
     return 0
+
 
 def batched_bound_s(spec, hbm_gbs, fma_tflops, projected):
     """Roofline time of one cell in the arrangement the batched form runs it

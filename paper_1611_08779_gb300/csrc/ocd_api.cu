@@ -252,11 +252,13 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
         h16 ? ocd::projected_h16_kernel_ptr(P.storage, U) : ocd::projected_tma_kernel_ptr(U);
     const size_t smem =
         h16 ? ocd::projected_h16_smem_per_cta(U) : ocd::projected_tma_smem_per_cta(U);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
+    const int tt = h16 ? nt : ocd::projected_tma_threads();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tt, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm >= 1) {
       long long grid = (long long)di.sms * per_sm;
-      if (grid > need) grid = need;
+      const long long need_t = (P.Nsc + tt / 32 - 1) / (tt / 32);  // one warp per subcarrier
+      if (grid > need_t) grid = need_t;
       e = h16 ? ocd::launch_projected_h16(P, (unsigned)grid, stream)
               : ocd::launch_projected_tma(P, (unsigned)grid, stream);
       if (e == cudaSuccess) e = cudaGetLastError();

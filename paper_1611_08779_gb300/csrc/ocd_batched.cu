@@ -34,7 +34,6 @@ static __device__ __align__(256) unsigned int g_static_tickets[OCD_STATIC_MAX_CE
 
 namespace {
 
-constexpr int kTmaThreads = 128;
 constexpr int kDefaultStepsPerTicket = 8;  // bulk-copy form: staged steps per ticket
 
 struct CellPlan {
@@ -84,7 +83,7 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
     cp.kind = 1;
     cp.ut = c.U <= 8 ? 1 : c.U <= 16 ? 2 : 4;
     cp.npp = cp.S = 0;
-    cp.nt = wide ? ocd::projected_wide_threads() : kTmaThreads;
+    cp.nt = wide ? ocd::projected_wide_threads() : ocd::projected_tma_threads();
     cp.smem = wide ? ocd::projected_wide_smem_per_cta() : ocd::projected_tma_smem_per_cta(c.U);
     int spt = te && te->sc_per_ticket > 0 ? te->sc_per_ticket : 0;
     if (spt == 0) {

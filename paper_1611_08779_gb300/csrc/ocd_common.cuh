@@ -79,6 +79,7 @@ constexpr int kProjectedMaxUsers = 8;
 constexpr int kTmaMaxUsers = 16;
 const void* projected_tma_kernel_ptr(int U);
 size_t projected_tma_smem_per_cta(int U);
+int projected_tma_threads();
 cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream);
 // Reads (and optionally clears) the fault word of the bulk-copy kernels;
 // synchronous with respect to the device.

@@ -32,8 +32,10 @@ const void* projected_tma_kernel_ptr(int U) {
 }
 
 size_t projected_tma_smem_per_cta(int U) {
-  return 4 * (U <= 8 ? TmaShape<1>::kWarpBytes : TmaShape<2>::kWarpBytes) + 1024;
+  return OCD_TMA_WARPS * (U <= 8 ? TmaShape<1>::kWarpBytes : TmaShape<2>::kWarpBytes) + 1024;
 }
+
+int projected_tma_threads() { return 32 * OCD_TMA_WARPS; }
 
 cudaError_t encode_ymap(const DetectParams& P, CUtensorMap* map) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -56,8 +58,8 @@ cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStrea
   if (e != cudaSuccess) return e;
   DetectParams p = P;
   void* args[] = {&p, &map};
-  return cudaLaunchKernel(projected_tma_kernel_ptr(P.U), dim3(grid), dim3(128), args,
-                          projected_tma_smem_per_cta(P.U), stream);
+  return cudaLaunchKernel(projected_tma_kernel_ptr(P.U), dim3(grid), dim3(projected_tma_threads()),
+                          args, projected_tma_smem_per_cta(P.U), stream);
 }
 
 int tma_steps_per_sc(int B, int T) {

@@ -46,6 +46,12 @@ namespace ocd {
 #ifndef OCD_TMA_STAGES
 #define OCD_TMA_STAGES 2      // staging buffers per warp (steps in flight + 1)
 #endif
+#ifndef OCD_TMA_WARPS
+#define OCD_TMA_WARPS 4       // warps per CTA
+#endif
+#ifndef OCD_TMA_PARTS
+#define OCD_TMA_PARTS 3       // accumulator parts per tile: 3 (hh, hl, lh) or 2 (hh, hl + lh)
+#endif
 
 // Users are padded to 8 * UT: an MMA tile has 16 rows = real and imaginary
 // parts of 8 users, and UT user tiles (1 or 2) cover up to 16 users.
@@ -162,8 +168,10 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
   // order (0,0), (0,1), (1,1).  Rows 0-7 hold real parts and rows 8-15
   // imaginary parts of user m*8 + gq.
   constexpr int NG = UT == 1 ? 1 : 3;
-  float qacc[UT][2][3][4];
-  float gacc[NG][3][4];
+  constexpr int NQ = OCD_TMA_PARTS;
+  static_assert(NQ == 2 || NQ == 3, "two or three accumulator parts");
+  float qacc[UT][2][NQ][4];
+  float gacc[NG][NQ][4];
 
   // prologue: the first kStages - 1 steps in flight
   Cursor cur{first, 0, 0};   // step being computed
@@ -213,13 +221,13 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
 #pragma unroll
         for (int n = 0; n < 2; ++n)
 #pragma unroll
-          for (int q = 0; q < 3; ++q)
+          for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int e = 0; e < 4; ++e) qacc[m][n][q][e] = 0.0f;
 #pragma unroll
       for (int n = 0; n < NG; ++n)
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < NQ; ++q)
 #pragma unroll
           for (int e = 0; e < 4; ++e) gacc[n][q][e] = 0.0f;
     }
@@ -257,16 +265,45 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
       split_tf32(ya.y, bh1, bl1);
       split_tf32(yc.x, ch0, cl0);
       split_tf32(yc.y, ch1, cl1);
+      if constexpr (NQ == 3) {
 #pragma unroll
-      for (int m = 0; m < UT; ++m) {
-        mma3_tf32(qacc[m][0], ah[m], al[m], bh0, bh1, bl0, bl1);
-        mma3_tf32(qacc[m][1], ah[m], al[m], ch0, ch1, cl0, cl1);
-        // G tile (m, n), n >= m: the B column j = n*8 + gq is h_j, i.e. this
-        // lane's A entries of user tile n (b0 = Re, b1 = Im).
-        if (decltype(with_g)::value) {
+        for (int m = 0; m < UT; ++m) {
+          mma3_tf32(qacc[m][0], ah[m], al[m], bh0, bh1, bl0, bl1);
+          mma3_tf32(qacc[m][1], ah[m], al[m], ch0, ch1, cl0, cl1);
+          // G tile (m, n), n >= m: the B column j = n*8 + gq is h_j, i.e. this
+          // lane's A entries of user tile n (b0 = Re, b1 = Im).
+          if (decltype(with_g)::value) {
 #pragma unroll
-          for (int n = m; n < UT; ++n)
-            mma3_tf32(gacc[m == 0 ? n : 2], ah[m], al[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+            for (int n = m; n < UT; ++n)
+              mma3_tf32(gacc[m == 0 ? n : 2], ah[m], al[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+          }
+        }
+      } else {
+        // two parts: round 1 (hi*hi, hi*lo) over every tile, then round 2
+        // (lo*hi into the hi*lo part, updated several MMAs earlier)
+#pragma unroll
+        for (int m = 0; m < UT; ++m) {
+          mma_tf32(qacc[m][0][0], ah[m][0], ah[m][1], ah[m][2], bh0, bh1);
+          mma_tf32(qacc[m][0][1], ah[m][0], ah[m][1], ah[m][2], bl0, bl1);
+          mma_tf32(qacc[m][1][0], ah[m][0], ah[m][1], ah[m][2], ch0, ch1);
+          mma_tf32(qacc[m][1][1], ah[m][0], ah[m][1], ah[m][2], cl0, cl1);
+          if (decltype(with_g)::value) {
+#pragma unroll
+            for (int n = m; n < UT; ++n) {
+              mma_tf32(gacc[m == 0 ? n : 2][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
+              mma_tf32(gacc[m == 0 ? n : 2][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < UT; ++m) {
+          mma_tf32(qacc[m][0][1], al[m][0], al[m][1], al[m][2], bh0, bh1);
+          mma_tf32(qacc[m][1][1], al[m][0], al[m][1], al[m][2], ch0, ch1);
+          if (decltype(with_g)::value) {
+#pragma unroll
+            for (int n = m; n < UT; ++n)
+              mma_tf32(gacc[m == 0 ? n : 2][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
+          }
         }
       }
     };
@@ -325,9 +362,10 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         for (int e = 0; e < 2; ++e) {
           const int ts = 8 * n + 2 * t + e;
           const int u = m * 8 + gq;
-          const float (&a)[3][4] = qacc[m][n];
-          sq[2 * (ts * NU + u)] = (a[2][e] + a[1][e]) + a[0][e];
-          sq[2 * (ts * NU + u) + 1] = (a[2][2 + e] + a[1][2 + e]) + a[0][2 + e];
+          const float (&a)[NQ][4] = qacc[m][n];
+          sq[2 * (ts * NU + u)] = (a[NQ - 1][e] + (NQ == 3 ? a[1][e] : 0.0f)) + a[0][e];
+          sq[2 * (ts * NU + u) + 1] =
+              (a[NQ - 1][2 + e] + (NQ == 3 ? a[1][2 + e] : 0.0f)) + a[0][2 + e];
         }
     if (first) {
 #pragma unroll
@@ -336,9 +374,9 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         for (int n = m; n < UT; ++n)
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            const float (&a)[3][4] = gacc[m == 0 ? n : 2];
-            const float re = (a[2][e] + a[1][e]) + a[0][e];
-            const float im = (a[2][2 + e] + a[1][2 + e]) + a[0][2 + e];
+            const float (&a)[NQ][4] = gacc[m == 0 ? n : 2];
+            const float re = (a[NQ - 1][e] + (NQ == 3 ? a[1][e] : 0.0f)) + a[0][e];
+            const float im = (a[NQ - 1][2 + e] + (NQ == 3 ? a[1][2 + e] : 0.0f)) + a[0][2 + e];
             const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
             sg[2 * (i * NU + j)] = re;
             sg[2 * (i * NU + j) + 1] = im;
@@ -457,7 +495,7 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
 // Single problem: warp gw of the persistent grid takes subcarriers gw,
 // gw + (warps in the grid), ...
 template <int UT>
-__global__ void __launch_bounds__(128, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
+__global__ void __launch_bounds__(32 * OCD_TMA_WARPS, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
 ocd_projected_tma_kernel(const __grid_constant__ DetectParams P,
                          const __grid_constant__ CUtensorMap ymap) {
   using S = TmaShape<UT>;
@@ -487,7 +525,7 @@ ocd_projected_tma_kernel(const __grid_constant__ DetectParams P,
 // ticket is a run of consecutive subcarriers of one cell.  Tickets of cell c
 // are [tick_end[c-1], tick_end[c]).
 template <int UT>
-__global__ void __launch_bounds__(128, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
+__global__ void __launch_bounds__(32 * OCD_TMA_WARPS, UT == 1 ? OCD_TMA_MIN_CTAS : 2)
 ocd_batched_tma_kernel(const __grid_constant__ BatchTable tab, unsigned int* __restrict__ tickets) {
   using S = TmaShape<UT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];

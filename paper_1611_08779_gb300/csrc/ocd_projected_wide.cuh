@@ -65,12 +65,18 @@ __device__ unsigned int g_wide_fault = 0;
 // Index of G tile (m, n), n >= m, among the 10 upper tiles.
 __host__ __device__ constexpr int wide_gtile(int m, int n) { return m * 4 - m * (m - 1) / 2 + (n - m); }
 
-// Two-part split product: d[0] += hi*hi, d[1] += hi*lo + lo*hi.
-__device__ __forceinline__ void mma2_tf32(float (&d)[2][4], const uint32_t (&ah)[3],
-                                          const uint32_t (&al)[3], uint32_t bh0, uint32_t bh1,
-                                          uint32_t bl0, uint32_t bl1) {
+// Two-part split product d[0] += hi*hi, d[1] += hi*lo + lo*hi, issued in two
+// rounds over all tiles of a k-step: round 1 (hi*hi, hi*lo) has no
+// dependence between consecutive MMAs; round 2 (lo*hi) adds to the d[1] that
+// round 1 updated several MMAs earlier, so no MMA waits on the one before.
+__device__ __forceinline__ void mma2_round1(float (&d)[2][4], const uint32_t (&ah)[3],
+                                            uint32_t bh0, uint32_t bh1, uint32_t bl0,
+                                            uint32_t bl1) {
   mma_tf32(d[0], ah[0], ah[1], ah[2], bh0, bh1);
   mma_tf32(d[1], ah[0], ah[1], ah[2], bl0, bl1);
+}
+__device__ __forceinline__ void mma2_round2(float (&d)[2][4], const uint32_t (&al)[3],
+                                            uint32_t bh0, uint32_t bh1) {
   mma_tf32(d[1], al[0], al[1], al[2], bh0, bh1);
 }
 
@@ -226,8 +232,12 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
           for (int m = 0; m < 4; ++m)
 #pragma unroll
             for (int n = m; n < 4; ++n)
-              mma2_tf32(acc[wide_gtile(m, n)], ah[m], al[m], ah[n][0], ah[n][2], al[n][0],
-                        al[n][2]);
+              mma2_round1(acc[wide_gtile(m, n)], ah[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int n = m; n < 4; ++n)
+              mma2_round2(acc[wide_gtile(m, n)], al[m], ah[n][0], ah[n][2]);
         }
       }
     } else {
@@ -249,8 +259,13 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
           split_tf32(yc.y, ch1, cl1);
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
-            mma2_tf32(acc[2 * m], ah[m], al[m], bh0, bh1, bl0, bl1);
-            mma2_tf32(acc[2 * m + 1], ah[m], al[m], ch0, ch1, cl0, cl1);
+            mma2_round1(acc[2 * m], ah[m], bh0, bh1, bl0, bl1);
+            mma2_round1(acc[2 * m + 1], ah[m], ch0, ch1, cl0, cl1);
+          }
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            mma2_round2(acc[2 * m], al[m], bh0, bh1);
+            mma2_round2(acc[2 * m + 1], al[m], ch0, ch1);
           }
         }
       }

@@ -473,6 +473,8 @@ __device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float
     uint32_t yh0, yl0, yh1, yl1;
     split_tf32(y.x, yh0, yl0);
     split_tf32(y.y, yh1, yl1);
+    // round 1: hi*hi and hi*lo of every tile (independent MMAs); round 2:
+    // lo*hi, added to a part round 1 updated several MMAs earlier
     int tile = 0;
 #pragma unroll
     for (int m = 0; m < UT; ++m) {
@@ -480,10 +482,16 @@ __device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float
       for (int n = m; n < UT; ++n, ++tile) {
         mma_tf32(g[tile][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
         mma_tf32(g[tile][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
-        mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
       }
       mma_tf32(qa[m][0], ah[m][0], ah[m][1], ah[m][2], yh0, yh1);
       mma_tf32(qa[m][1], ah[m][0], ah[m][1], ah[m][2], yl0, yl1);
+    }
+    tile = 0;
+#pragma unroll
+    for (int m = 0; m < UT; ++m) {
+#pragma unroll
+      for (int n = m; n < UT; ++n, ++tile)
+        mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
       mma_tf32(qa[m][1], al[m][0], al[m][1], al[m][2], yh0, yh1);
     }
   }

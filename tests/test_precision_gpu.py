@@ -107,3 +107,37 @@ def test_storage_error_vs_float_inputs_is_small_at_moderate_snr():
         torch.cuda.synchronize()
         agree = np.mean((L.cpu().numpy() > 0) == (L_ref > 0))
         assert agree > 0.995, (dtype, agree)
+
+
+def test_error_per_snr_against_the_fp64_reference(capsys):
+    """The precision-form system (256x16, K = 4, 64-QAM, T = 14): per SNR
+    0..30 dB, the error of each storage against the FP64 oracle on the
+    unquantized inputs (what 16-bit storage costs), printed as a table."""
+    import math
+    rows = []
+    for snr in range(0, 31, 5):
+        d = synth.make_uplink(48, 256, 16, 14, 64, float(snr), 100 + snr, dtype=np.complex128)
+        z_ref, l_ref = orc.ocd_detect(d["H"], d["Y"], d["N0"], 1.0, 4, orc.BOX, 64)
+        for name, dt in (("f32", None), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+            if dt is None:
+                H = torch.from_numpy(d["H"].astype(np.complex64)).cuda()
+                Y = torch.from_numpy(d["Y"].astype(np.complex64)).cuda()
+            else:
+                H, _ = quantize(d["H"], dt)
+                Y, _ = quantize(d["Y"], dt)
+            x, L = ocd.ocd_detect(H, Y, d["N0"], 1.0, 4, "box", 64)
+            torch.cuda.synchronize()
+            x = x.cpu().numpy()
+            L = L.cpu().numpy()
+            xe = float(np.max(np.linalg.norm(x - z_ref, axis=-1)
+                              / np.maximum(np.linalg.norm(z_ref, axis=-1), 1e-3 * math.sqrt(16))))
+            le = float(np.quantile(np.abs(L - l_ref) / np.maximum(np.abs(l_ref), 1.0), 0.99))
+            mm = float(np.mean((L > 0) != (l_ref > 0)))
+            rows.append((snr, name, xe, le, mm))
+            bound = {"f32": (1e-4, 1e-3, 1e-3), "bf16": (1e-2, 5e-2, 5e-3),
+                     "f16": (2e-3, 1e-2, 1e-3)}[name]
+            assert xe <= bound[0] and le <= bound[1] and mm <= bound[2], (snr, name, xe, le, mm)
+    with capsys.disabled():
+        print("\nSNR dB  storage  xhat rel err max  LLR rel err p99  hard-bit mismatch")
+        for snr, name, xe, le, mm in rows:
+            print(f"{snr:6d}  {name:7s}  {xe:16.2e}  {le:15.2e}  {mm:17.2e}")
