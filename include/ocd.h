@@ -225,18 +225,22 @@ int ocd_detect_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tu
                        void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
- * ocd_detect_batched_static -- ocd_detect_batched without a caller
- * workspace and without any allocation: the ticket counters live in a
- * library-owned device array of OCD_STATIC_MAX_CELLS entries (1 KiB per
- * device), so ncells is limited to OCD_STATIC_MAX_CELLS (OCD_ERR_UNSUPPORTED
- * beyond, nothing enqueued).  The paper has no counterpart; this is a
- * serving convenience.  The counters are zeroed on `stream` at the start of
- * every call.  Races: all calls on one device share the counters, so calls
- * must not overlap in time -- issue them on one stream or order them with
- * events (concurrent calls on unordered streams give wrong results).  The
- * first call on a device looks up the array's address and sets up the
- * device's kernel attributes; make that call outside stream capture, after
- * which the call is capturable like ocd_detect_batched.
+ * ocd_detect_batched_static -- ocd_detect_batched for callers that cannot
+ * allocate device memory: a plug-in running inside a host application that
+ * owns the CUDA context and all of its memory, a process whose device memory
+ * is taken up front by another allocator, or a latency-critical loop that
+ * cannot afford cudaMalloc's implicit synchronization.  It takes no
+ * workspace and allocates nothing (no cudaMalloc, no cudaFree, no library
+ * allocation): its ticket counters live in a library-owned device array of
+ * OCD_STATIC_MAX_CELLS entries (1 KiB), which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart.
+ *   ncells      0..OCD_STATIC_MAX_CELLS; more gives OCD_ERR_UNSUPPORTED and
+ *               nothing is enqueued.  Other arguments as ocd_detect_batched.
+ * The counters are zeroed on `stream` at the start of every call.  All calls
+ * on one device share them, so calls that overlap on the GPU race and give
+ * wrong results: issue them on one stream, or order them with events.  The
+ * first call on a device looks up the array's device address and sets up the
+ * device's kernel attributes; make that first call before any stream capture.
  */
 #define OCD_STATIC_MAX_CELLS 256
 int ocd_detect_batched_static(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,

@@ -147,11 +147,14 @@ def ocd_detect_batched(cells, tune: Tune | None = None, workspace: torch.Tensor 
 
 def ocd_detect_batched_static(cells, tune: Tune | None = None,
                               stream: torch.cuda.Stream | None = None):
-    """ocd_detect_batched with the library's static ticket counters: no
-    workspace and no allocation (outputs must already be in the cells), at
-    most OCD_STATIC_MAX_CELLS cells, and calls on one device must not overlap
-    in time (use one stream).  Make the first call on a device outside CUDA
-    graph capture."""
+    """ocd_detect_batched for callers that cannot allocate device memory
+    (the host application owns the context and its memory, or cudaMalloc's
+    synchronization is not acceptable): no workspace, nothing allocated here
+    or in the library (outputs must already be in the cells).  At most
+    OCD_STATIC_MAX_CELLS cells; the library's counters are shared by every
+    call on a device, so calls that overlap on the GPU race (use one stream).
+    The first call on a device looks up the counters' address: make it
+    before any stream capture."""
     lib = _native.load()
     arr, dev = _cell_array(cells)
     if arr is None:

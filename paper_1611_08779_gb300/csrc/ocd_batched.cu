@@ -28,8 +28,11 @@
 
 using namespace ocdh;
 
-// Ticket counters of ocd_detect_batched_static (1 KiB per device): one per
-// launch, and a call makes at most one launch per non-empty cell.
+// Ticket counters of ocd_detect_batched_static, the entry point for callers
+// that cannot allocate device memory (1 KiB, held by every GPU that loads
+// the library): one per launch, and a call makes at most one launch per
+// non-empty cell.  Host code must not pass this name to a kernel (it is the
+// host-side stand-in); static_scratch() gives the device address.
 static __device__ __align__(256) unsigned int g_static_tickets[OCD_STATIC_MAX_CELLS];
 
 namespace {

@@ -1,7 +1,11 @@
-"""ocd_detect_batched_static (library-owned ticket counters, no workspace,
-no allocation) against ocd_detect_batched on the same cells: two calls in a
-row give bit-identical results, the counters start from zero on every call,
-nothing is allocated, and oversized batches are rejected before any work."""
+"""ocd_detect_batched_static, the entry point for callers that cannot
+allocate device memory (their host application owns the context and its
+memory, or cudaMalloc's synchronization is not acceptable): it keeps its
+ticket counters in a library-owned device array.  Checked through the C ABI
+against ocd_detect_batched on the same cells: two calls in a row give
+bit-identical results (the counters are cleared on every call), nothing is
+allocated, and oversized batches are rejected before any work.  This file is
+collected last, and passes alone or after the rest of the suite."""
 import numpy as np
 import pytest
 
