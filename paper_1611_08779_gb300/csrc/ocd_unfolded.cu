@@ -71,6 +71,12 @@ __device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) 
   p = d * n;
 }
 
+// 8-byte asynchronous copy global -> shared (completed by cp.async.wait_all).
+__device__ __forceinline__ void async_copy8(float2* dst, const float2* src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
 // Column stride (complex elements) of the user-major channel copy in shared
 // memory: 32 NA + 1, so the transposing stores of one warp spread over the
 // banks and the column loads (lane b reads antenna b) are conflict-free.
@@ -84,8 +90,10 @@ struct Warp {
   float2* sH;        // SMEM: this warp's user-major copy [U][staged_stride], zero padded
   int lane;
 
-  // Copies H[w] into sH (coalesced reads, transposed stores).
-  __device__ __forceinline__ void stage() const {
+  // Copies H[w] into sH (coalesced reads, transposed stores) and, when ysrc
+  // is given, B received values into sy, with asynchronous 8-byte copies
+  // (cp.async), so that all of a lane's loads are in flight at once.
+  __device__ __forceinline__ void stage(const float2* ysrc = nullptr, float2* sy = nullptr) const {
     if (!SMEM) return;
     constexpr int st = staged_stride<NA>();
     __syncwarp();  // the previous sample's reads are done
@@ -93,8 +101,11 @@ struct Warp {
     for (int e = lane; e < n; e += 32) {
       const int b = e / P.U;
       const int u = e - b * P.U;
-      sH[u * st + b] = __ldg(Hw + e);
+      async_copy8(sH + u * st + b, Hw + e);
     }
+    if (ysrc)
+      for (int b = lane; b < P.B; b += 32) async_copy8(sy + b, ysrc + b);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
   }
 
@@ -519,8 +530,11 @@ __device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float
   }
 }
 
-template <int NA>
-__global__ void __launch_bounds__(128)
+// UT: 8-user MMA tiles of the Gram product (1, 2 or 4); one instance each,
+// so that a small U does not carry the register budget of 32 users.  Two
+// warps per CTA: the per-warp channel copy bounds the warps per SM.
+template <int NA, int UT>
+__global__ void __launch_bounds__(64)
 ocd_unfolded_proj_forward_kernel(const __grid_constant__ UnfoldParams P) {
   extern __shared__ float2 unf_smem[];
   constexpr int st = staged_stride<NA>();
@@ -537,13 +551,9 @@ ocd_unfolded_proj_forward_kernel(const __grid_constant__ UnfoldParams P) {
        s += nw) {
     const long long w = s / P.T;
     Warp<NA, true> W{P, P.H + w * B * U, sH, lane};
-    W.stage();  // ends with __syncwarp
-    for (int b = lane; b < B; b += 32) sy[b] = __ldg(P.Y + s * B + b);
-    __syncwarp();
+    W.stage(P.Y + s * B, sy);  // ends with __syncwarp
     // G = H^H H and q0 = H^H y on the tensor cores
-    if (U <= 8) gram_q0_tf32<1, NA>(sH, sy, sG, U, B, lane);
-    else if (U <= 16) gram_q0_tf32<2, NA>(sH, sy, sG, U, B, lane);
-    else gram_q0_tf32<4, NA>(sH, sy, sG, U, B, lane);
+    gram_q0_tf32<UT, NA>(sH, sy, sG, U, B, lane);
     __syncwarp();
     float2 q = lane < U ? sy[lane] : make_float2(0.0f, 0.0f);  // q0 (written over y)
     const float nrm = lane < U ? sG[lane * gst + lane].x : 0.0f;
@@ -636,11 +646,19 @@ ocd_unfolded_proj_backward_kernel(const __grid_constant__ UnfoldParams P) {
       float2 zb = make_float2(0.0f, 0.0f), qs = zb;
       qsweep<true>(P, sG, gst, lane, q, z, d, p, om, zb, qs);
       float om_l = 0.0f, al_l = 0.0f;  // lane u accumulates the terms of user u
+      // hs (lane l) = G[:, l]^H q' = sum_j conj(G[j][l]) q'_j, kept current:
+      // an update changes only q'_u (by dq), which adds conj(G[u][l]) dq to
+      // every hs_l, so no reduction over the users is needed per update.
+      float2 hs = make_float2(0.0f, 0.0f);
+      for (int j = 0; j < U; ++j) {
+        const float2 qj = shfl2(qbar, j);
+        const float2 g = lane < U ? sG[j * gst + lane] : make_float2(0.0f, 0.0f);
+        hs.x = fmaf(g.x, qj.x, fmaf(g.y, qj.y, hs.x));
+        hs.y = fmaf(g.x, qj.y, fmaf(-g.y, qj.x, hs.y));
+      }
       for (int u = U - 1; u >= 0; --u) {
-        const float2 g = lane < U ? sG[lane * gst + u] : make_float2(0.0f, 0.0f);
-        // G[:, u]^H q'  (conj(G[j][u]) q'_j summed over j)
-        float2 hr = make_float2(fmaf(g.x, qbar.x, g.y * qbar.y), fmaf(g.x, qbar.y, -g.y * qbar.x));
-        hr = warp_sum2(hr);
+        const float2 hr = hs;  // lane u: G[:, u]^H q'
+        float2 dq = make_float2(0.0f, 0.0f);
         if (lane == u) {
           const float wr0 = fmaf(d, qs.x, p * zb.x);
           const float wi0 = fmaf(d, qs.y, p * zb.y);
@@ -655,9 +673,14 @@ ocd_unfolded_proj_backward_kernel(const __grid_constant__ UnfoldParams P) {
           om_l = fmaf(cr - zb.x, gr, fmaf(ci - zb.y, gi, om_l));
           const float wbr = mr * om * gr, wbi = mi * om * gi;
           zbar = make_float2(zbar.x - om * gr + p * wbr, zbar.y - om * gi + p * wbi);
-          qbar = make_float2(fmaf(d, wbr, qbar.x), fmaf(d, wbi, qbar.y));
+          dq = make_float2(d * wbr, d * wbi);
+          qbar = make_float2(qbar.x + dq.x, qbar.y + dq.y);
           al_l -= d * d * fmaf(qs.x, wbr, qs.y * wbi) + p * d * fmaf(zb.x, wbr, zb.y * wbi);
         }
+        dq = shfl2(dq, u);
+        const float2 g = lane < U ? sG[u * gst + lane] : make_float2(0.0f, 0.0f);
+        hs.x = fmaf(g.x, dq.x, fmaf(g.y, dq.y, hs.x));
+        hs.y = fmaf(g.x, dq.y, fmaf(-g.y, dq.x, hs.y));
       }
       float om_bar = warp_sum(om_l);
       float al_bar = warp_sum(al_l);
@@ -686,16 +709,31 @@ cudaError_t allow_smem(const void* fn, size_t smem) {
   return e;
 }
 
-template <int NA>
-cudaError_t launch_proj(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
-  const size_t smem = backward ? 4ull * P.U * (P.U + 1) * sizeof(float2)
-                               : 4ull * proj_warp_elems<NA>(P.U) * sizeof(float2);
-  const void* fn = backward ? reinterpret_cast<const void*>(ocd_unfolded_proj_backward_kernel)
-                            : reinterpret_cast<const void*>(ocd_unfolded_proj_forward_kernel<NA>);
+constexpr int kProjFwdWarps = 2;  // warps per CTA of the projected forward kernel
+
+template <int NA, int UT>
+cudaError_t launch_proj_fwd(const UnfoldParams& P, cudaStream_t stream) {
+  const size_t smem = (size_t)kProjFwdWarps * proj_warp_elems<NA>(P.U) * sizeof(float2);
+  const void* fn = reinterpret_cast<const void*>(ocd_unfolded_proj_forward_kernel<NA, UT>);
   cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  if (backward) ocd_unfolded_proj_backward_kernel<<<grid, 128, smem, stream>>>(P);
-  else ocd_unfolded_proj_forward_kernel<NA><<<grid, 128, smem, stream>>>(P);
+  const unsigned grid = (unsigned)((P.samples + kProjFwdWarps - 1) / kProjFwdWarps);
+  ocd_unfolded_proj_forward_kernel<NA, UT><<<grid, 32 * kProjFwdWarps, smem, stream>>>(P);
+  return cudaGetLastError();
+}
+
+template <int NA>
+cudaError_t launch_proj(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
+  if (!backward) {
+    if (P.U <= 8) return launch_proj_fwd<NA, 1>(P, stream);
+    if (P.U <= 16) return launch_proj_fwd<NA, 2>(P, stream);
+    return launch_proj_fwd<NA, 4>(P, stream);
+  }
+  const size_t smem = 4ull * P.U * (P.U + 1) * sizeof(float2);
+  const void* fn = reinterpret_cast<const void*>(ocd_unfolded_proj_backward_kernel);
+  cudaError_t e = allow_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  ocd_unfolded_proj_backward_kernel<<<grid, 128, smem, stream>>>(P);
   return cudaGetLastError();
 }
 
