@@ -71,6 +71,15 @@ __device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) 
   p = d * n;
 }
 
+// Lane mapping for copying a row-major [n][U] complex array with a warp:
+// `rows` = max(1, 32 / U) rows per step, lane -> row r0 (< rows for an
+// active lane) and column u.
+__device__ __forceinline__ void row_lane(int U, int lane, int& rows, int& r0, int& u) {
+  rows = U >= 32 ? 1 : 32 / U;
+  r0 = lane / U;
+  u = lane - r0 * U;
+}
+
 // 8-byte asynchronous copy global -> shared (completed by cp.async.wait_all).
 __device__ __forceinline__ void async_copy8(float2* dst, const float2* src) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -97,12 +106,13 @@ struct Warp {
     if (!SMEM) return;
     constexpr int st = staged_stride<NA>();
     __syncwarp();  // the previous sample's reads are done
-    const int n = P.B * P.U;
-    for (int e = lane; e < n; e += 32) {
-      const int b = e / P.U;
-      const int u = e - b * P.U;
-      async_copy8(sH + u * st + b, Hw + e);
-    }
+    // lane -> (row r0 of a group of `rows` channel rows, user u): the rows
+    // of a group are contiguous in H, so each copy instruction reads one
+    // contiguous run; no division inside the loop
+    int rows, r0, u;
+    row_lane(P.U, lane, rows, r0, u);
+    if (r0 < rows)
+      for (int b = r0; b < P.B; b += rows) async_copy8(sH + u * st + b, Hw + b * P.U + u);
     if (ysrc)
       for (int b = lane; b < P.B; b += 32) async_copy8(sy + b, ysrc + b);
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -558,7 +568,12 @@ ocd_unfolded_proj_forward_kernel(const __grid_constant__ UnfoldParams P) {
     float2 q = lane < U ? sy[lane] : make_float2(0.0f, 0.0f);  // q0 (written over y)
     const float nrm = lane < U ? sG[lane * gst + lane].x : 0.0f;
     float2* ckG = P.ckpt + ckpt_g(P, s);
-    for (int e = lane; e < U * U; e += 32) ckG[e] = sG[(e / U) * gst + (e % U)];
+    {
+      int rows, r0, u;
+      row_lane(U, lane, rows, r0, u);
+      if (r0 < rows)
+        for (int i = r0; i < U; i += rows) ckG[i * U + u] = sG[i * gst + u];
+    }
     float2 z = make_float2(0.0f, 0.0f), zb = z, qs = z;
     for (int k = 0; k < P.K; ++k) {
       if (lane < U) {
@@ -599,7 +614,12 @@ ocd_unfolded_proj_backward_kernel(const __grid_constant__ UnfoldParams P) {
     const long long w = s / P.T;
     __syncwarp();
     const float2* ckG = P.ckpt + ckpt_g(P, s);
-    for (int e = lane; e < U * U; e += 32) sG[(e / U) * gst + (e % U)] = ckG[e];
+    {
+      int rows, r0, u;
+      row_lane(U, lane, rows, r0, u);
+      if (r0 < rows)
+        for (int i = r0; i < U; i += rows) sG[i * gst + u] = ckG[i * U + u];
+    }
     __syncwarp();
     const float nrm = lane < U ? sG[lane * gst + lane].x : 0.0f;
     // ---- adjoint of the soft output and of xhat (lane u)
