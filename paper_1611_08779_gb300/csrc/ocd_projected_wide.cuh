@@ -16,9 +16,10 @@
 //
 // Each accumulator tile keeps two parts, hi*hi and hi*lo + lo*hi of the
 // three-term TF32 split, summed once per phase.  One warp per CTA (the
-// per-warp staging, q, G and preprocessing areas take 37 KB of shared
-// memory); the channel block is therefore read once per phase, the second
-// time from L2.
+// per-warp staging, G and preprocessing areas take 21 KB of shared memory
+// with 16-antenna blocks; q0 reuses the staging buffer of the step being
+// finished); the channel block is read once per phase, the second time
+// from L2.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (type only; no driver library is linked)
@@ -35,11 +36,14 @@ namespace ocd {
 #ifndef OCD_WIDE_STAGES
 #define OCD_WIDE_STAGES 2     // staging buffers per warp
 #endif
+#ifndef OCD_WIDE_BLOCK
+#define OCD_WIDE_BLOCK 16     // antennas per staged block (16 or 32)
+#endif
 
 struct WideShape {
   static constexpr int kUsers = 32;                         // user slots (4 MMA tiles)
   static constexpr int kPass = 16;                          // symbols per q0 pass
-  static constexpr int kBB = 32;                            // antennas per staged block
+  static constexpr int kBB = OCD_WIDE_BLOCK;                // antennas per staged block
   static constexpr int kBoxAnt = 16;                        // antennas per Y box (128 B rows)
   static constexpr int kBoxBytes = kPass * 128;
   static constexpr int kBoxes = kBB / kBoxAnt;
@@ -48,8 +52,12 @@ struct WideShape {
   static constexpr int kBufBytes = kYBytes + kHBytes;       // multiple of 1024
   static constexpr int kStages = OCD_WIDE_STAGES;
   static constexpr int kUP = kUsers / 2;                    // users per sweep lane
-  static constexpr int kOffQ = kStages * kBufBytes;         // q0, later z [pass symbol][u]
-  static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;  // G [i][j]
+  // q0, later z [pass symbol][u] (8 kPass kUsers bytes) lives in the staging
+  // buffer of the step whose epilogue uses it: that buffer receives its next
+  // copy only when the following step starts
+  static constexpr int kQBytes = 8 * kPass * kUsers;
+  static_assert(kQBytes <= kBufBytes, "q0 fits in a staging buffer");
+  static constexpr int kOffG = kStages * kBufBytes;         // G [i][j]
   static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
   static constexpr int kOffBar = kOffPre + 16 * kUsers;
   static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
@@ -92,7 +100,6 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
   constexpr int UP = S::kUP;
   constexpr int NU = S::kUsers;
   const int lane = threadIdx.x & 31;
-  float* sq = reinterpret_cast<float*>(ws + S::kOffQ);
   float* sg = reinterpret_cast<float*>(ws + S::kOffG);
   float* spre = reinterpret_cast<float*>(ws + S::kOffPre);
 
@@ -309,6 +316,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
     }
 
     // ---------------- q0 epilogue, sweeps, outputs ------------------------
+    // this step's staging buffer is consumed (the products above are done)
+    float* sq = reinterpret_cast<float*>(ws + this_buf * S::kBufBytes);
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
