@@ -30,6 +30,13 @@ namespace ocd {
 // exactly one translation unit (ocd_projected_h16.cu) includes this header.
 __device__ unsigned int g_h16_fault = 0;
 
+#ifndef OCD_H16_STAGES
+#define OCD_H16_STAGES 3      // staging buffers per warp
+#endif
+#ifndef OCD_H16_MIN_CTAS
+#define OCD_H16_MIN_CTAS 4    // resident CTAs per SM of the one-tile instance (registers <= 128)
+#endif
+
 template <int UT>
 struct H16Shape {
   static constexpr int kUsers = 8 * UT;                    // user slots
@@ -38,7 +45,7 @@ struct H16Shape {
   static constexpr int kYBytes = kPass * 128;              // one swizzled Y box (64 x 16)
   static constexpr int kHBytes = kBB * kUsers * 4;         // staged H block
   static constexpr int kBufBytes = ((kYBytes + kHBytes + 1023) / 1024) * 1024;
-  static constexpr int kStages = 3;
+  static constexpr int kStages = OCD_H16_STAGES;
   static constexpr int kUP = kUsers / 2;                   // users per sweep lane
   static constexpr int kOffQ = kStages * kBufBytes;        // q0, later z [pass symbol][u]
   static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;
@@ -72,7 +79,7 @@ __device__ __forceinline__ uint32_t swap_neg(uint32_t v) {
 }
 
 template <int STORE, int UT>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, UT == 1 ? OCD_H16_MIN_CTAS : 3)
 ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorMap ymap) {
   using S = H16Shape<UT>;
   constexpr int BB = S::kBB;
