@@ -59,8 +59,12 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *                       16-byte aligned with even B (float32 storage) or
  *                       B % 4 == 0 (16-bit storage); U <= 32 with float32
  *                       storage, even B and 16-byte aligned H and Y.
- *   OCD_ALGO_AUTO       PROJECTED when it supports the shape and T >= 2 (or
- *                       U > 16), else RESIDUAL.
+ *   OCD_ALGO_AUTO       PROJECTED when it supports the shape and either
+ *                       T >= 2, or T == 1 with float32 storage, even B and
+ *                       16-byte aligned H and Y; else RESIDUAL.
+ * For T == 1 and U <= 8 (float32 storage, even B, 16-byte aligned H and Y)
+ * the projected form runs with one lane per subcarrier (G and q0 accumulated
+ * in registers, no reduction across lanes).
  */
 typedef enum { OCD_ALGO_AUTO = 0, OCD_ALGO_RESIDUAL = 1, OCD_ALGO_PROJECTED = 2 } ocd_algo_t;
 

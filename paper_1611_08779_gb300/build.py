@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libocd.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ocd_api.cu", "ocd_batched.cu", "ocd_unfolded.cu", "ocd_residual.cu", "ocd_projected.cu", "ocd_projected_tma.cu", "ocd_projected_wide.cu",
+SOURCES = ["ocd_api.cu", "ocd_batched.cu", "ocd_unfolded.cu", "ocd_residual.cu", "ocd_projected.cu", "ocd_projected_tma.cu", "ocd_projected_wide.cu", "ocd_projected_lane.cu",
            "ocd_projected_h16.cu"]
 
 

@@ -118,6 +118,11 @@ int device_info(int dev, DeviceInfo& out) {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
+    for (int u = 1; u <= ocd::kLaneMaxUsers; ++u) {
+      e = cudaFuncSetAttribute(ocd::projected_lane_kernel_ptr(u),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
     for (const void* fn : {ocd::projected_wide_kernel_ptr(),
                            reinterpret_cast<const void*>(ocd::batched_wide_kernel())}) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
@@ -213,17 +218,26 @@ bool can_wide(const ocd::DetectParams& P) {
   return P.storage == ocd::kStoreC64 && P.U > ocd::kTmaMaxUsers && P.U <= ocd::kWideMaxUsers &&
          P.B % 2 == 0 && aligned16(P);
 }
+// One lane per subcarrier: one symbol, float32 storage, U <= 8, even B,
+// 16-byte aligned bases.
+bool can_lane(const ocd::DetectParams& P) {
+  return P.storage == ocd::kStoreC64 && P.T == 1 && P.U <= ocd::kLaneMaxUsers &&
+         P.B % 2 == 0 && aligned16(P);
+}
 bool can_projected(const ocd::DetectParams& P) {
   return can_tma32(P) || can_wide(P) || can_h16(P) || P.U <= ocd::kProjectedMaxUsers;
 }
 
 // Algorithm choice for OCD_ALGO_AUTO: the projected form wins whenever its
-// two per-subcarrier products are shared by more than one symbol.
-// Above 16 users the residual form's staged channel leaves the SMs nearly
-// idle, so the (four-tile) projected form wins even for one symbol.
+// two per-subcarrier products are shared by more than one symbol.  For one
+// symbol it still wins in its bulk-copy and one-lane-per-subcarrier kernels
+// (measured at 32x8, 128x8 and 128x16, T = 1); the load-based projected
+// kernel keeps the residual form for T = 1.
 int resolve_algo(int algo, const ocd::DetectParams& P) {
   if (algo != OCD_ALGO_AUTO) return algo;
-  return (can_projected(P) && (P.T >= 2 || can_wide(P))) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  const bool one_symbol_ok = can_lane(P) || can_tma32(P) || can_wide(P);
+  return (can_projected(P) && (P.T >= 2 || one_symbol_ok)) ? OCD_ALGO_PROJECTED
+                                                          : OCD_ALGO_RESIDUAL;
 }
 
 int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
@@ -231,6 +245,22 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
   const long long need = (P.Nsc + nt / 32 - 1) / (nt / 32);  // one warp per subcarrier
   int per_sm = 0;
   cudaError_t e;
+  if (can_lane(P)) {
+    const void* fn = ocd::projected_lane_kernel_ptr(U);
+    const int lt = ocd::projected_lane_threads();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, lt,
+                                                      ocd::projected_lane_smem_per_cta(U));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm >= 1) {
+      long long grid = (long long)di.sms * per_sm;
+      const long long need_l = (ocd::projected_lane_groups(P.Nsc) + lt / 32 - 1) / (lt / 32);
+      if (grid > need_l) grid = need_l;  // one warp per group of 32 subcarriers
+      e = ocd::launch_projected_lane(P, (unsigned)grid, stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "projected kernel launch");
+      return OCD_OK;
+    }
+  }
   if (can_wide(P)) {
     const void* fn = ocd::projected_wide_kernel_ptr();
     const int wt = ocd::projected_wide_threads();

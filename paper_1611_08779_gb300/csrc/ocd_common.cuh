@@ -91,6 +91,15 @@ const void* projected_h16_kernel_ptr(int storage, int U);
 size_t projected_h16_smem_per_cta(int U);
 cudaError_t launch_projected_h16(const DetectParams& P, unsigned grid, cudaStream_t stream);
 cudaError_t projected_h16_fault(unsigned int* bits, bool clear);
+// One-symbol projected kernels (T = 1, U <= 8, float32 storage, even B,
+// 16-byte aligned H and Y): one lane per subcarrier, one warp per group of
+// 32 consecutive subcarriers (128 threads per CTA).
+constexpr int kLaneMaxUsers = 8;
+const void* projected_lane_kernel_ptr(int U);
+size_t projected_lane_smem_per_cta(int U);
+int projected_lane_threads();
+long long projected_lane_groups(long long Nsc);
+cudaError_t launch_projected_lane(const DetectParams& P, unsigned grid, cudaStream_t stream);
 // Launches one warp that waits, with the same bounded wait the bulk-copy
 // kernels use, on an mbarrier phase nothing completes; the wait expires
 // after wait_ns and sets the fault word.  Exercises the timeout path.
