@@ -485,6 +485,7 @@ def run_ours(args):
                 "value", "unit", "ms_per_step", "arms_gbps", "roofline", "config"))
             line["unfolded_form"] = form_summary(measure_unfolded, args, (
                 "value", "unit", "ms_per_step", "forward_ms", "roofline", "config"))
+            line["single_symbol_form"] = form_summary(measure_single, args, ("forms",))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_line(args)
         print(json.dumps(line), flush=True)
@@ -560,6 +561,85 @@ def run_precision(args):
             "forms": out, "accuracy_per_snr_db": per_snr,
             "accuracy_sample": "480 subcarriers x 14 symbols per SNR; 16-bit forms against the "
                                "float32-storage result, and uncoded BER against the sent bits"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+SINGLE_CONFIGS = (  # (B, U, order, subcarriers per frame of --frames)
+    (128, 8, 64, 4000),
+    (32, 8, 16, 12000),
+)
+
+
+def measure_single(args):
+    """One symbol per channel (T = 1, K = 3, OCD-BOX at 15 dB): 128x8 64-QAM
+    and 32x8 16-QAM, whose inputs (frames x 4000 and frames x 12000
+    subcarriers: 758 MB and 599 MB at 20 frames) stream from HBM; the
+    one-lane-per-subcarrier projected kernel (what AUTO runs) against the
+    HBM roofline, with the residual form beside it."""
+    import torch
+
+    import paper_1611_08779_gb300 as ocd
+    from paper_1611_08779_gb300 import synth
+    dev = torch.device("cuda", 0)
+    peak = float(measured_peaks()[0].get("hbm_gbs", FALLBACK_HBM_GBS))
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    for b, u, order, per_frame in SINGLE_CONFIGS:
+        q = int(round(math.log2(order)))
+        nsc = per_frame * args.frames
+        d = synth.make_uplink(nsc, b, u, 1, order, SNR_DB, seed=21)
+        H = torch.from_numpy(d["H"]).to(dev)
+        Y = torch.from_numpy(d["Y"]).to(dev)
+        del d["H"], d["Y"]
+        x = torch.empty((nsc, 1, u), dtype=torch.complex64, device=dev)
+        llr = torch.empty((nsc, 1, u, q), dtype=torch.float32, device=dev)
+        arms = {}
+        for algo in ("auto", "residual"):
+            def step():
+                ocd.ocd_detect(H, Y, d["N0"], 1.0, K, args.mode, order, xhat=x, llr=llr,
+                               algo=algo, stream=stream)
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    step()
+            torch.cuda.synchronize(dev)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            steps = args.steps if algo == "auto" else max(3, args.steps // 4)
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                for _ in range(steps):
+                    step()
+                ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            arms[algo] = ev0.elapsed_time(ev1) / steps
+        ms = arms["auto"]
+        nbytes = algorithmic_bytes_per_sc(b, u, 1, q) * nsc
+        achieved = nbytes / (ms / 1e3) / 1e9
+        out[f"{b}x{u}"] = {
+            "value": nsc * u * q / (ms / 1e3) / 1e9, "unit": "Gb/s", "ms_per_step": ms,
+            "config": {"B": b, "U": u, "T": 1, "K": K, "qam": order, "mode": args.mode,
+                       "subcarriers_per_step": nsc},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "kernel": "ocd_projected_lane_kernel",
+                         "algorithmic_bytes_per_launch": nbytes},
+            "residual_form": {"value": nsc * u * q / (arms["residual"] / 1e3) / 1e9,
+                              "unit": "Gb/s", "ms_per_step": arms["residual"]},
+        }
+        del H, Y, x, llr
+    return {"metric": "detected Gb/s, one symbol per channel (T=1, K=3)", "forms": out,
+            "value": out["128x8"]["value"], "unit": "Gb/s",
+            "ms_per_step": out["128x8"]["ms_per_step"]}
+
+
+def run_single(args):
+    res = measure_single(args)
+    line = {"metric": res["metric"], "workload": "single", "value": res["value"], "unit": "Gb/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "OCD-BOX T=1 K=3: 128x8 64-QAM and 32x8 16-QAM",
+                       "l2": "inputs larger than L2 (no flush)"},
+            "forms": res["forms"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -792,11 +872,13 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and unfolded forms in the headline line")
-    ap.add_argument("--workload", choices=["metric", "precision", "batched", "unfolded"], default="metric",
+    ap.add_argument("--workload", choices=["metric", "precision", "batched", "unfolded", "single"],
+                    default="metric",
                     help="metric: the headline 128x8 configuration; precision: 256x16 K=4 in "
                          "float32 / bfloat16 / float16 storage with per-SNR accuracy; batched: "
                          "mixed cells in one persistent launch; unfolded: differentiable OCD-BOX "
-                         "forward + adjoint (128x16, K=5, 4096 samples)")
+                         "forward + adjoint (128x16, K=5, 4096 samples); single: one symbol per "
+                         "channel (T=1: 128x8 64-QAM, 32x8 16-QAM)")
     ap.add_argument("--cells", type=int, default=24, help="cells of the batched workload")
     ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
                     help="seconds of clock sampling the timed steps are extended to")
@@ -811,6 +893,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "unfolded":
         return run_unfolded(args)
+    if args.workload == "single":
+        return run_single(args)
     return run_ours(args)
 
 

@@ -252,9 +252,14 @@ int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStre
                                                       ocd::projected_lane_smem_per_cta(U));
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm >= 1) {
-      long long grid = (long long)di.sms * per_sm;
-      const long long need_l = (ocd::projected_lane_groups(P.Nsc) + lt / 32 - 1) / (lt / 32);
-      if (grid > need_l) grid = need_l;  // one warp per group of 32 subcarriers
+      // one warp per group of 32 subcarriers, as many as the SMs hold
+      // (measured: cutting the warp count to even out the last round of
+      // groups loses more than the last round costs)
+      const int wpc = lt / 32;
+      const long long groups = ocd::projected_lane_groups(P.Nsc);
+      const long long wmax = (long long)di.sms * per_sm * wpc;
+      const long long warps = groups < wmax ? groups : wmax;
+      const long long grid = (warps + wpc - 1) / wpc;
       e = ocd::launch_projected_lane(P, (unsigned)grid, stream);
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "projected kernel launch");

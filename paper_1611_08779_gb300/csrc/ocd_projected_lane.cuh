@@ -53,6 +53,7 @@ struct LaneShape {
   static constexpr int kYPieces = kYBytes / 16;
   static_assert(kAPC >= 2 && kHBytes % 16 == 0 && kYBytes % 16 == 0, "16-byte pieces");
   static_assert(kHPitch % 32 == 16 && kYPitch % 32 == 16, "odd multiples of 16 bytes");
+  static_assert(kHBytes >= 16 * U, "a row holds z, ||h||^2 and p of every user");
 };
 
 __device__ __forceinline__ void lane_copy16(uint32_t dst, const void* src) {
@@ -88,6 +89,9 @@ __global__ void __launch_bounds__(128, OCD_LANE_MIN_CTAS) ocd_projected_lane_ker
   // Copies of step (group g, chunk c) into stage buffer `buf`.  Piece p of
   // the group's H (y) block is piece p % kHPieces of subcarrier p / kHPieces;
   // pieces past the chunk's antennas (last chunk) or past Nsc are skipped.
+  // When the pieces of a subcarrier divide 32 a lane copies the same piece j
+  // of every (32 / pieces)-th subcarrier, so its offsets advance by constants.
+  const int BU = B * U;
   auto issue = [&](long long g, int c, int buf) {
     unsigned char* hb = ws + buf * S::kStageBytes;
     unsigned char* yb = hb + 32 * S::kHPitch;
@@ -97,22 +101,37 @@ __global__ void __launch_bounds__(128, OCD_LANE_MIN_CTAS) ocd_projected_lane_ker
     const int nsc = (int)min(32LL, Nsc - sc0);
     const int hvalid = bb * U / 2;  // 16-byte pieces of H per subcarrier (bb even)
     const int yvalid = bb / 2;
+    const float2* hsrc = P.H + (sc0 * B + b0) * U;
+    const float2* ysrc = P.Y + sc0 * B + b0;
+    if constexpr (32 % S::kHPieces == 0) {
+      constexpr int SPI = 32 / S::kHPieces;
+      const int s0 = lane / S::kHPieces, j = lane % S::kHPieces;
+      if (j < hvalid) {
 #pragma unroll
-    for (int i = 0; i < S::kHPieces; ++i) {
-      const int p = lane + 32 * i;
-      const int s = p / S::kHPieces, j = p - s * S::kHPieces;
-      if (s < nsc && j < hvalid) {
-        const float2* src = P.H + ((sc0 + s) * B + b0) * U + 2 * j;
-        lane_copy16(lane_smem(hb + s * S::kHPitch + 16 * j), src);
+        for (int i = 0; i < S::kHPieces; ++i) {
+          const int sj = s0 + SPI * i;
+          if (sj < nsc) lane_copy16(lane_smem(hb + sj * S::kHPitch + 16 * j), hsrc + sj * BU + 2 * j);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < S::kHPieces; ++i) {
+        const int p = lane + 32 * i;
+        const int sj = p / S::kHPieces, j = p - sj * S::kHPieces;
+        if (sj < nsc && j < hvalid)
+          lane_copy16(lane_smem(hb + sj * S::kHPitch + 16 * j), hsrc + sj * BU + 2 * j);
       }
     }
+    static_assert(32 % S::kYPieces == 0, "y pieces per subcarrier divide 32");
+    {
+      constexpr int SPI = 32 / S::kYPieces;
+      const int s0 = lane / S::kYPieces, j = lane % S::kYPieces;
+      if (j < yvalid) {
 #pragma unroll
-    for (int i = 0; i < S::kYPieces; ++i) {
-      const int p = lane + 32 * i;
-      const int s = p / S::kYPieces, j = p - s * S::kYPieces;
-      if (s < nsc && j < yvalid) {
-        const float2* src = P.Y + (sc0 + s) * B + b0 + 2 * j;
-        lane_copy16(lane_smem(yb + s * S::kYPitch + 16 * j), src);
+        for (int i = 0; i < S::kYPieces; ++i) {
+          const int sj = s0 + SPI * i;
+          if (sj < nsc) lane_copy16(lane_smem(yb + sj * S::kYPitch + 16 * j), ysrc + sj * B + 2 * j);
+        }
       }
     }
   };
@@ -230,9 +249,17 @@ __global__ void __launch_bounds__(128, OCD_LANE_MIN_CTAS) ocd_projected_lane_ker
           for (int u = 0; u < U; ++u) P.xhat[sc * U + u] = make_float2(zr[u], zi[u]);
         }
         if (P.llr) {
+          // z, ||h_u||^2 and p_u go to this lane's own row of the consumed
+          // stage buffer (rewritten only after the next __syncwarp), so that
+          // one rolled loop over the users holds the only copy of the LLR code
+          float4* zrow = reinterpret_cast<float4*>(ws + buf * S::kStageBytes + lane * S::kHPitch);
 #pragma unroll
-          for (int u = 0; u < U; ++u)
-            user_llr(make_float2(zr[u], zi[u]), gr[u][u], pv[u], P, P.llr + (sc * U + u) * P.Q);
+          for (int u = 0; u < U; ++u) zrow[u] = make_float4(zr[u], zi[u], gr[u][u], pv[u]);
+#pragma unroll 1
+          for (int u = 0; u < U; ++u) {
+            const float4 v = zrow[u];
+            user_llr(make_float2(v.x, v.y), v.z, v.w, P, P.llr + (sc * U + u) * P.Q);
+          }
         }
       }
     }
