@@ -177,9 +177,9 @@ int ocd_wait_selftest(int limit_us, cudaStream_t stream);
 
 /* One cell: the arguments of ocd_detect_typed.  `algo` (ocd_algo_t):
  * OCD_ALGO_AUTO takes the tune table's choice for the cell's shape, else the
- * default (PROJECTED for float32 storage, U <= 16, even B, 16-byte aligned H
- * and Y, and T >= 2; else RESIDUAL).  The batched PROJECTED form needs
- * exactly those conditions (OCD_ERR_UNSUPPORTED otherwise). */
+ * default (PROJECTED for float32 storage, U <= 32, even B and 16-byte
+ * aligned H and Y, at any T; else RESIDUAL).  The batched PROJECTED form
+ * needs exactly those conditions (OCD_ERR_UNSUPPORTED otherwise). */
 typedef struct {
   const void* H;
   const void* Y;

@@ -77,8 +77,9 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   int algo = c.algo;
   if (algo == OCD_ALGO_AUTO && te && (te->algo == OCD_ALGO_RESIDUAL || te->algo == OCD_ALGO_PROJECTED))
     algo = te->algo;
-  if (algo == OCD_ALGO_AUTO)
-    algo = (tma_ok && (c.T >= 2 || wide)) ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  // default without a tune entry: the bulk-copy projected form wherever it
+  // applies, one symbol included (as the single-problem path at T = 1)
+  if (algo == OCD_ALGO_AUTO) algo = tma_ok ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
   if (algo == OCD_ALGO_PROJECTED && !tma_ok)
     return fail(OCD_ERR_UNSUPPORTED, "batched projected form needs float32 storage, even B "
                 "and 16-byte aligned H and Y (U=%d B=%d)", c.U, c.B);
