@@ -199,7 +199,8 @@ typedef struct {
   int algo;              /* OCD_ALGO_RESIDUAL or OCD_ALGO_PROJECTED */
   int symbols_per_item;  /* residual form: symbols per work item, 1 or 2 */
   int lanes_per_item;    /* residual form: lanes per work item, power of two <= 32 */
-  int sc_per_ticket;     /* projected form: subcarriers per ticket, 1..256 */
+  int sc_per_ticket;     /* projected form: subcarriers per ticket, 1..256 (0 when
+                            T == 1 and U <= 8: the one-lane kernel has no tile) */
   float time_us;         /* tuning measurement of this choice (informative) */
 } ocd_tune_entry_t;
 
@@ -216,9 +217,10 @@ size_t ocd_batched_workspace_size(int ncells);
 /*
  * ocd_detect_batched -- detects `ncells` cells (0..OCD_MAX_CELLS) in one
  * enqueue: a zeroing of the workspace's ticket counters, then one persistent
- * launch per kernel variant the cells need (at most 32 cells per launch),
- * on up to four internal streams ordered after `stream` on entry and before
- * it on exit.  `workspace`: caller-owned device memory of at least
+ * launch per kernel variant the cells need (at most 32 cells per launch;
+ * a projected-form cell with T == 1 and U <= 8 gets a launch of its own of
+ * the one-lane-per-subcarrier kernel), on up to four internal streams
+ * ordered after `stream` on entry and before it on exit.  `workspace`: caller-owned device memory of at least
  * ocd_batched_workspace_size(ncells) bytes, 4-byte aligned, not used by
  * another call in flight.  `tune` may be NULL.  Cells with Nsc*T == 0 are
  * skipped.  Argument errors name the offending cell; nothing is enqueued

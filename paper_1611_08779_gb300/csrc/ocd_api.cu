@@ -240,27 +240,37 @@ int resolve_algo(int algo, const ocd::DetectParams& P) {
                                                           : OCD_ALGO_RESIDUAL;
 }
 
+int lane_grid(const ocd::DetectParams& P, const DeviceInfo& di, unsigned& grid) {
+  grid = 0;
+  const void* fn = ocd::projected_lane_kernel_ptr(P.U);
+  const int lt = ocd::projected_lane_threads();
+  int per_sm = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, fn, lt, ocd::projected_lane_smem_per_cta(P.U));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (per_sm < 1) return OCD_OK;
+  // one warp per group of 32 subcarriers, as many as the SMs hold
+  // (measured: cutting the warp count to even out the last round of groups
+  // loses more than the last round costs)
+  const int wpc = lt / 32;
+  const long long groups = ocd::projected_lane_groups(P.Nsc);
+  const long long wmax = (long long)di.sms * per_sm * wpc;
+  const long long warps = groups < wmax ? groups : wmax;
+  grid = (unsigned)((warps + wpc - 1) / wpc);
+  return OCD_OK;
+}
+
 int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
   const int nt = 128;
   const long long need = (P.Nsc + nt / 32 - 1) / (nt / 32);  // one warp per subcarrier
   int per_sm = 0;
   cudaError_t e;
   if (can_lane(P)) {
-    const void* fn = ocd::projected_lane_kernel_ptr(U);
-    const int lt = ocd::projected_lane_threads();
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, lt,
-                                                      ocd::projected_lane_smem_per_cta(U));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm >= 1) {
-      // one warp per group of 32 subcarriers, as many as the SMs hold
-      // (measured: cutting the warp count to even out the last round of
-      // groups loses more than the last round costs)
-      const int wpc = lt / 32;
-      const long long groups = ocd::projected_lane_groups(P.Nsc);
-      const long long wmax = (long long)di.sms * per_sm * wpc;
-      const long long warps = groups < wmax ? groups : wmax;
-      const long long grid = (warps + wpc - 1) / wpc;
-      e = ocd::launch_projected_lane(P, (unsigned)grid, stream);
+    unsigned grid = 0;
+    const int st = lane_grid(P, di, grid);
+    if (st != OCD_OK) return st;
+    if (grid > 0) {
+      e = ocd::launch_projected_lane(P, grid, stream);
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "projected kernel launch");
       return OCD_OK;

@@ -41,7 +41,7 @@ constexpr int kDefaultStepsPerTicket = 8;  // bulk-copy form: staged steps per t
 
 struct CellPlan {
   int index;              // position in the caller's list
-  int kind;               // 0 residual, 1 bulk-copy projected
+  int kind;               // 0 residual, 1 bulk-copy projected, 2 one lane per subcarrier
   int npp, S, nt, ut;     // kernel instance
   size_t smem;
   ocd::DetectParams P;
@@ -83,6 +83,19 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   if (algo == OCD_ALGO_PROJECTED && !tma_ok)
     return fail(OCD_ERR_UNSUPPORTED, "batched projected form needs float32 storage, even B "
                 "and 16-byte aligned H and Y (U=%d B=%d)", c.U, c.B);
+  if (algo == OCD_ALGO_PROJECTED && can_lane(cp.P)) {
+    // one symbol, U <= 8: the single-problem path's one-lane-per-subcarrier
+    // kernel, launched for this cell alone (same kernel, same results)
+    cp.kind = 2;
+    cp.ut = c.U;
+    cp.npp = cp.S = 0;
+    cp.nt = ocd::projected_lane_threads();
+    cp.smem = ocd::projected_lane_smem_per_cta(c.U);
+    cp.sc_per_tick = 0;
+    cp.tickets = 0;
+    cp.work = (double)c.Nsc * (8.0 * c.B * c.U + 8.0 * c.B + 12.0 * c.U);
+    return OCD_OK;
+  }
   if (algo == OCD_ALGO_PROJECTED) {
     cp.kind = 1;
     cp.ut = c.U <= 8 ? 1 : c.U <= 16 ? 2 : 4;
@@ -133,7 +146,9 @@ struct Launch {
   int nt;
   size_t smem;
   double work;
-  std::unique_ptr<ocd::BatchTable> tab;
+  std::unique_ptr<ocd::BatchTable> tab;  // persistent launches: the cell table
+  bool single = false;                   // one-cell launch with parameters P
+  ocd::DetectParams P;
 };
 
 // Plans every cell and groups them into launches (heaviest first).
@@ -158,6 +173,22 @@ int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
   std::vector<bool> taken(plans.size(), false);
   for (size_t i = 0; i < plans.size(); ++i) {
     if (taken[i]) continue;
+    if (plans[i].kind == 2) {
+      taken[i] = true;
+      Launch L;
+      L.single = true;
+      L.P = plans[i].P;
+      L.fn = ocd::projected_lane_kernel_ptr(plans[i].P.U);
+      L.nt = plans[i].nt;
+      L.smem = plans[i].smem;
+      L.work = plans[i].work;
+      const int st = lane_grid(L.P, di, L.grid);
+      if (st != OCD_OK) return st;
+      if (L.grid == 0)
+        return fail(OCD_ERR_UNSUPPORTED, "cell %d: one-lane kernel cannot be resident", plans[i].index);
+      launches.push_back(std::move(L));
+      continue;
+    }
     std::vector<size_t> fam;
     for (size_t j = i; j < plans.size(); ++j)
       if (!taken[j] && same_family(plans[i], plans[j])) {
@@ -250,11 +281,18 @@ int enqueue(std::vector<Launch>& launches, void* workspace, cudaStream_t stream)
   unsigned int* counters = static_cast<unsigned int*>(workspace);
   cudaError_t e = cudaMemsetAsync(counters, 0, launches.size() * sizeof(unsigned int), stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  if (launches.size() == 1) {
-    Launch& L = launches[0];
-    unsigned int* ctr = counters;
+  // a persistent launch takes (cell table, its ticket counter); a one-cell
+  // launch takes the cell's parameters
+  auto launch = [&](Launch& L, unsigned int* ctr, cudaStream_t s) {
+    if (L.single) {
+      void* args[] = {&L.P};
+      return cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, s);
+    }
     void* args[] = {L.tab.get(), &ctr};
-    e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, stream);
+    return cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, s);
+  };
+  if (launches.size() == 1) {
+    e = launch(launches[0], counters, stream);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
     return OCD_OK;
   }
@@ -273,10 +311,7 @@ int enqueue(std::vector<Launch>& launches, void* workspace, cudaStream_t stream)
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
   }
   for (size_t i = 0; i < launches.size(); ++i) {
-    Launch& L = launches[i];
-    unsigned int* ctr = counters + i;
-    void* args[] = {L.tab.get(), &ctr};
-    e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, hs->s[i % ns]);
+    e = launch(launches[i], counters + i, hs->s[i % ns]);
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
   }
   for (int i = 0; i < ns; ++i) {
@@ -432,7 +467,18 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
                    g.xhat, g.llr, Pg);
       tma_all = tma_all && (can_tma32(Pg) || can_wide(Pg));
     }
-    if (tma_all && c.T >= 1) {
+    bool lane_all = true;
+    for (const ocd_cell_t& g : group) {
+      ocd::DetectParams Pg;
+      build_params(g.H, g.Y, g.storage, g.Nsc, g.B, g.U, g.T, g.N0, g.Es, g.K, g.mode, al,
+                   g.xhat, g.llr, Pg);
+      lane_all = lane_all && can_lane(Pg);
+    }
+    if (lane_all) {  // the one-lane kernel has no tile to choose
+      ocd_tune_entry_t t = base;
+      t.algo = OCD_ALGO_PROJECTED;
+      cand.push_back(t);
+    } else if (tma_all && c.T >= 1) {
       for (int spt : {1, 2, 4, 8, 16, 32}) {
         ocd_tune_entry_t t = base;
         t.algo = OCD_ALGO_PROJECTED;

@@ -51,7 +51,12 @@ int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl
               int L_req);
 
 bool can_tma32(const ocd::DetectParams& P);  // U <= 16
+bool can_lane(const ocd::DetectParams& P);   // T == 1, U <= 8: one lane per subcarrier
 bool can_wide(const ocd::DetectParams& P);   // 16 < U <= 32
+
+// Grid of the one-lane-per-subcarrier kernel for P (0 when it cannot be
+// resident on the device).
+int lane_grid(const ocd::DetectParams& P, const DeviceInfo& di, unsigned& grid);
 
 // Internal streams (per device, created once) shared by the host-buffer path
 // and the batched form; the caller holds g_hs_mu for the whole enqueue.

@@ -94,7 +94,9 @@ def test_autotuned_tiles_keep_parity():
     for e in tune.entries:
         assert e["algo"] in (1, 2) and e["time_us"] > 0
         if e["algo"] == 2:
-            assert e["U"] <= 32 and e["sc_per_ticket"] >= 1
+            # one symbol with U <= 8 runs the one-lane kernel: no ticket size
+            lane = e["T"] == 1 and e["U"] <= 8
+            assert e["U"] <= 32 and (e["sc_per_ticket"] == 0 if lane else e["sc_per_ticket"] >= 1)
         else:
             assert e["symbols_per_item"] in (1, 2) and e["lanes_per_item"] >= 1
     for c in cells:
