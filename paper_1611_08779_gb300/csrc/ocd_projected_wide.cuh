@@ -36,6 +36,12 @@ namespace ocd {
 #ifndef OCD_WIDE_STAGES
 #define OCD_WIDE_STAGES 2     // staging buffers per warp
 #endif
+#ifndef OCD_WIDE_MIN_CTAS
+#define OCD_WIDE_MIN_CTAS 1  // resident CTAs (= warps) per SM the register budget targets
+#endif
+#ifndef OCD_WIDE_F32X2
+#define OCD_WIDE_F32X2 1  // sweeps on packed FP32 pairs of users
+#endif
 #ifndef OCD_WIDE_BLOCK
 #define OCD_WIDE_BLOCK 16     // antennas per staged block (16 or 32)
 #endif
@@ -64,6 +70,27 @@ struct WideShape {
   static constexpr int kThreads = 32;                       // one warp per CTA
   static_assert(kBufBytes % 1024 == 0, "swizzled boxes need 1024-byte alignment");
 };
+
+// G in shared memory, row i as [Re G_i0 .. Re G_i(NU-1) | Im G_i0 .. Im G_i(NU-1)]:
+// a sweep lane reads the real and the imaginary parts of its users as
+// separate runs (16-byte aligned for 4 consecutive users).
+__device__ __forceinline__ int wide_gre(int i, int j) { return i * 2 * WideShape::kUsers + j; }
+__device__ __forceinline__ int wide_gim(int i, int j) {
+  return i * 2 * WideShape::kUsers + WideShape::kUsers + j;
+}
+// Packed FP32 pairs (fma.rn.f32x2: two independent IEEE fmas).
+__device__ __forceinline__ unsigned long long wide_pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void wide_unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void wide_fma2(unsigned long long& d, unsigned long long a,
+                                          unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
 
 // Fault word of the wide kernels (bit 0: a wait timed out; bit 1: a batched
 // cell's tensor map was misaligned).  Defined here because exactly one
@@ -292,16 +319,16 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
             const float re = a[1][e] + a[0][e];
             const float im = a[1][2 + e] + a[0][2 + e];
             const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
-            sg[2 * (i * NU + j)] = re;
-            sg[2 * (i * NU + j) + 1] = im;
+            sg[wide_gre(i, j)] = re;
+            sg[wide_gim(i, j)] = im;
             if (n != m) {
-              sg[2 * (j * NU + i)] = re;
-              sg[2 * (j * NU + i) + 1] = -im;
+              sg[wide_gre(j, i)] = re;
+              sg[wide_gim(j, i)] = -im;
             }
           }
       __syncwarp();
       {
-        const float nrm = sg[2 * (lane * NU + lane)];
+        const float nrm = sg[wide_gre(lane, lane)];
         const float den = nrm + P.alpha;
         const float dinv = (lane < U && den > 0.0f) ? 1.0f / den : 0.0f;
         const float p = dinv * nrm;
@@ -309,7 +336,7 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
         spre[4 * lane + 1] = p;
         spre[4 * lane + 2] = nrm;
         spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
-        sg[2 * (lane * NU + lane) + 1] = 0.0f;  // G_uu is real
+        sg[wide_gim(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
       continue;
@@ -331,6 +358,86 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
           sq[2 * (ts * NU + u) + 1] = a[1][2 + e] + a[0][2 + e];
         }
     __syncwarp();
+#if OCD_WIDE_F32X2
+    {
+      // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts; q as
+      // packed pairs of consecutive users, updated with fma.rn.f32x2 (each
+      // half one IEEE fma: the same operations, in the same order, as the
+      // scalar form)
+      const int ts = lane >> 1;
+      const int hf = lane & 1;
+      const bool act = ts < np;
+      unsigned long long QR[UP / 2], QI[UP / 2];
+      float zr[UP], zi[UP];
+#pragma unroll
+      for (int l2 = 0; l2 < UP / 2; ++l2) {
+        const int j = hf * UP + 2 * l2;
+        QR[l2] = act ? wide_pack2(sq[2 * (ts * NU + j)], sq[2 * (ts * NU + j + 1)]) : 0ull;
+        QI[l2] = act ? wide_pack2(sq[2 * (ts * NU + j) + 1], sq[2 * (ts * NU + j + 1) + 1]) : 0ull;
+        zr[2 * l2] = zr[2 * l2 + 1] = 0.0f;
+        zi[2 * l2] = zi[2 * l2 + 1] = 0.0f;
+      }
+      const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
+      const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
+      for (int k = 0; k < P.K; ++k) {
+#pragma unroll 1
+        for (int oh = 0; oh < 2; ++oh) {
+#pragma unroll
+        for (int lu = 0; lu < UP; ++lu) {
+          const int u = oh * UP + lu;
+          if (u < U) {
+            const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
+            float q0, q1, p0, p1;
+            wide_unpack2(QR[lu >> 1], q0, q1);
+            wide_unpack2(QI[lu >> 1], p0, p1);
+            const float qr = (lu & 1) ? q1 : q0;
+            const float qi = (lu & 1) ? p1 : p0;
+            float wr = fmaf(dp.x, qr, dp.y * zr[lu]);
+            float wi = fmaf(dp.x, qi, dp.y * zi[lu]);
+            wr = fminf(fmaxf(wr, -are), are);
+            wi = fminf(fmaxf(wi, -aim), aim);
+            const float dr0 = wr - zr[lu];
+            const float di0 = wi - zi[lu];
+            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+            const int owner = (lane & ~1) | oh;
+            const float dr = __shfl_sync(kFullMask, dr0, owner);
+            const float di = __shfl_sync(kFullMask, di0, owner);
+            const unsigned long long DR = wide_pack2(dr, dr);
+            const unsigned long long NDR = wide_pack2(-dr, -dr);
+            const unsigned long long NDI = wide_pack2(-di, -di);
+            const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
+            const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
+#pragma unroll
+            for (int l4 = 0; l4 < UP / 4; ++l4) {
+              const float4 r4 = gre[l4], i4 = gim[l4];
+              const unsigned long long re0 = wide_pack2(r4.x, r4.y), re1 = wide_pack2(r4.z, r4.w);
+              const unsigned long long im0 = wide_pack2(i4.x, i4.y), im1 = wide_pack2(i4.z, i4.w);
+              // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
+              wide_fma2(QR[2 * l4], im0, NDI);
+              wide_fma2(QR[2 * l4], re0, NDR);
+              wide_fma2(QI[2 * l4], im0, DR);
+              wide_fma2(QI[2 * l4], re0, NDI);
+              wide_fma2(QR[2 * l4 + 1], im1, NDI);
+              wide_fma2(QR[2 * l4 + 1], re1, NDR);
+              wide_fma2(QI[2 * l4 + 1], im1, DR);
+              wide_fma2(QI[2 * l4 + 1], re1, NDI);
+            }
+          }
+        }
+        }
+      }
+      __syncwarp();
+      if (act) {
+#pragma unroll
+        for (int l = 0; l < UP; ++l) {
+          const int j = hf * UP + l;
+          sq[2 * (ts * NU + j)] = zr[l];
+          sq[2 * (ts * NU + j) + 1] = zi[l];
+        }
+      }
+      __syncwarp();
+    }
+#else
     {
       // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts
       const int ts = lane >> 1;
@@ -367,15 +474,18 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
             const int owner = (lane & ~1) | oh;
             const float dr = __shfl_sync(kFullMask, dr0, owner);
             const float di = __shfl_sync(kFullMask, di0, owner);
-            const float4* gu = reinterpret_cast<const float4*>(sg + 2 * (u * NU + hf * UP));
+            const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
+            const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
 #pragma unroll
-            for (int l2 = 0; l2 < UP / 2; ++l2) {
-              const float4 g2 = gu[l2];
-              const int l = 2 * l2;
-              qr[l] = fmaf(-g2.x, dr, fmaf(-g2.y, di, qr[l]));
-              qi[l] = fmaf(-g2.x, di, fmaf(g2.y, dr, qi[l]));
-              qr[l + 1] = fmaf(-g2.z, dr, fmaf(-g2.w, di, qr[l + 1]));
-              qi[l + 1] = fmaf(-g2.z, di, fmaf(g2.w, dr, qi[l + 1]));
+            for (int l4 = 0; l4 < UP / 4; ++l4) {
+              const float4 r4 = gre[l4], i4 = gim[l4];
+              const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int l = 4 * l4 + c;
+                qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
+                qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
+              }
             }
           }
         }
@@ -392,6 +502,7 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
       }
       __syncwarp();
     }
+#endif
     for (int f = lane; f < np * U; f += 32) {
       const int ts = f / U;
       const int u = f - ts * U;
@@ -416,7 +527,7 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
 }
 
 // Single problem: warp (= CTA) b takes subcarriers b, b + gridDim.x, ...
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32, OCD_WIDE_MIN_CTAS)
 ocd_projected_wide_kernel(const __grid_constant__ DetectParams P,
                           const __grid_constant__ CUtensorMap ymap) {
   using S = WideShape;
@@ -438,7 +549,7 @@ ocd_projected_wide_kernel(const __grid_constant__ DetectParams P,
 
 // Several problems: each warp draws tickets (runs of subcarriers of one
 // cell) from a device counter, as ocd_batched_tma_kernel.
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32, OCD_WIDE_MIN_CTAS)
 ocd_batched_wide_kernel(const __grid_constant__ BatchTable tab, unsigned int* __restrict__ tickets) {
   using S = WideShape;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
