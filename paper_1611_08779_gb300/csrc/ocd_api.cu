@@ -124,7 +124,8 @@ int device_info(int dev, DeviceInfo& out) {
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
     for (const void* fn : {ocd::projected_wide_kernel_ptr(),
-                           reinterpret_cast<const void*>(ocd::batched_wide_kernel())}) {
+                           reinterpret_cast<const void*>(ocd::batched_wide_kernel(false)),
+                           reinterpret_cast<const void*>(ocd::batched_wide_kernel(true))}) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }

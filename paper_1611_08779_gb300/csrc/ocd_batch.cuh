@@ -56,7 +56,10 @@ const void* projected_wide_kernel_ptr();
 size_t projected_wide_smem_per_cta();
 int projected_wide_threads();
 cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStream_t stream);
-BatchFn batched_wide_kernel();
+// T <= 8: the 32-user kernels accumulate q0 in the G phase (the batched
+// kernel instance then takes only such cells).
+bool wide_fuses(int T);
+BatchFn batched_wide_kernel(bool fused);
 cudaError_t projected_wide_fault(unsigned int* bits, bool clear);
 
 }  // namespace ocd

@@ -43,6 +43,7 @@ struct CellPlan {
   int index;              // position in the caller's list
   int kind;               // 0 residual, 1 bulk-copy projected, 2 one lane per subcarrier
   int npp, S, nt, ut;     // kernel instance
+  bool fused;             // 32-user kernel with q0 in the G phase (T <= 8)
   size_t smem;
   ocd::DetectParams P;
   long long tickets;
@@ -69,6 +70,7 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
                     c.qam_order, c.xhat, c.llr, c.algo, al);
   if (st != OCD_OK) return st;
   cp.index = index;
+  cp.fused = false;
   build_params(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode, al, c.xhat,
                c.llr, cp.P);
   const ocd_tune_entry_t* te = force ? force : find_tune(tune, c);
@@ -99,6 +101,7 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   if (algo == OCD_ALGO_PROJECTED) {
     cp.kind = 1;
     cp.ut = c.U <= 8 ? 1 : c.U <= 16 ? 2 : 4;
+    cp.fused = wide && ocd::wide_fuses(c.T);
     cp.npp = cp.S = 0;
     cp.nt = wide ? ocd::projected_wide_threads() : ocd::projected_tma_threads();
     cp.smem = wide ? ocd::projected_wide_smem_per_cta() : ocd::projected_tma_smem_per_cta(c.U);
@@ -137,7 +140,8 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
 }
 
 bool same_family(const CellPlan& a, const CellPlan& b) {
-  return a.kind == b.kind && a.npp == b.npp && a.S == b.S && a.nt == b.nt && a.ut == b.ut;
+  return a.kind == b.kind && a.npp == b.npp && a.S == b.S && a.nt == b.nt && a.ut == b.ut &&
+         a.fused == b.fused;
 }
 
 struct Launch {
@@ -202,7 +206,7 @@ int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
       memset(L.tab.get(), 0, sizeof(ocd::BatchTable));
       const CellPlan& f = plans[fam[a]];
       L.fn = f.kind == 0 ? reinterpret_cast<const void*>(ocd::batched_residual_kernel(f.npp, f.S))
-             : f.ut == 4 ? reinterpret_cast<const void*>(ocd::batched_wide_kernel())
+             : f.ut == 4 ? reinterpret_cast<const void*>(ocd::batched_wide_kernel(f.fused))
                          : reinterpret_cast<const void*>(ocd::batched_tma_kernel(f.ut == 1 ? 8 : 16));
       L.nt = f.nt;
       L.smem = 0;

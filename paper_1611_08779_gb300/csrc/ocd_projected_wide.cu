@@ -22,7 +22,11 @@ cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStre
                           projected_wide_smem_per_cta(), stream);
 }
 
-BatchFn batched_wide_kernel() { return ocd_batched_wide_kernel; }
+bool wide_fuses(int T) { return OCD_WIDE_FUSE && T <= 8; }
+
+BatchFn batched_wide_kernel(bool fused) {
+  return fused ? ocd_batched_wide_kernel<true> : ocd_batched_wide_kernel<false>;
+}
 
 cudaError_t projected_wide_fault(unsigned int* bits, bool clear) {
   cudaError_t e = cudaMemcpyFromSymbol(bits, g_wide_fault, sizeof(unsigned int));

@@ -39,6 +39,9 @@ namespace ocd {
 #ifndef OCD_WIDE_MIN_CTAS
 #define OCD_WIDE_MIN_CTAS 1  // resident CTAs (= warps) per SM the register budget targets
 #endif
+#ifndef OCD_WIDE_FUSE
+#define OCD_WIDE_FUSE 1  // T <= 8: q0 accumulated in the G phase (no q0 pass)
+#endif
 #ifndef OCD_WIDE_F32X2
 #define OCD_WIDE_F32X2 1  // sweeps on packed FP32 pairs of users
 #endif
@@ -119,6 +122,7 @@ __device__ __forceinline__ void mma2_round2(float (&d)[2][4], const uint32_t (&a
 // problem P (ymap: Y as [Nsc*T][2B] floats, box 32 x 16, 128-byte swizzle).
 // Staging area and barriers persist across calls as in tma_walk; returns
 // false when a wait timed out.
+template <bool FUSED>
 __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorMap* ymap,
                                           unsigned char* ws, uint32_t bar0, uint32_t& parity,
                                           long long first, long long end, long long stride) {
@@ -142,7 +146,10 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
   for (int kk = 0; kk < 4; ++kk)
     yoff[kk] = gq * 128 + (((kk | ((t >> 1) << 2)) ^ gq) << 4) + ((t & 1) << 3);
   const int nblk = (B + BB - 1) / BB;
-  const int npasses = (T + S::kPass - 1) / S::kPass;
+  // FUSED (T <= 8, one n-tile of symbols): q0 is accumulated in the G phase
+  // from the same channel fragments, and there is no separate q0 pass
+  constexpr bool fused = FUSED;
+  const int npasses = fused ? 0 : (T + S::kPass - 1) / S::kPass;
   const long long steps_per_sc = (long long)(npasses + 1) * nblk;
   const long long my_nsc = first < end ? (end - 1 - first) / stride + 1 : 0;
   const long long nsteps = my_nsc * steps_per_sc;
@@ -168,13 +175,13 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
     const int bb = min(BB, B - b0);
     const uint32_t bar = bar0 + 8 * buf;
     unsigned char* bp = ws + buf * S::kBufBytes;
-    const int nbox = q.phase == 0 ? 0 : (bb + S::kBoxAnt - 1) / S::kBoxAnt;
+    const int nbox = (q.phase == 0 && !fused) ? 0 : (bb + S::kBoxAnt - 1) / S::kBoxAnt;
     if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nbox * S::kBoxBytes + bb * U * 8));
     __syncwarp();
     fence_proxy_async();
     if (lane < nbox)
       tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), ymap, 2 * (b0 + S::kBoxAnt * lane),
-                  (int)(q.sc * T + (q.phase - 1) * S::kPass), bar);
+                  (int)(q.sc * T + (fused ? 0 : (q.phase - 1) * S::kPass)), bar);
     if (lane == 31) {
       const float2* src = P.H + (q.sc * (long long)B + b0) * U;
       bulk_g2s(smem_addr(bp + S::kYBytes), src, (uint32_t)(bb * U * 8), bar);
@@ -182,8 +189,10 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
   };
 
   // acc[i]: G tile i (G phase) or q0 tile 2m + n (q0 passes); rows 0-7 real
-  // and 8-15 imaginary parts of user m*8 + gq.
+  // and 8-15 imaginary parts of user m*8 + gq.  qf[m]: q0 tile (m, 0) of the
+  // fused G phase.
   float acc[10][2][4];
+  float qf[4][2][4];
 
   Cursor cur{first, 0, 0};
   Cursor nxt{first, 0, 0};
@@ -215,8 +224,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
     const int phase = cur.phase;
     const int blk = cur.blk;
     const int bb = min(BB, B - blk * BB);
-    const int tb = (phase - 1) * S::kPass;
-    const int np = phase == 0 ? 0 : min(S::kPass, T - tb);
+    const int tb = fused ? 0 : (phase - 1) * S::kPass;
+    const int np = fused ? T : phase == 0 ? 0 : min(S::kPass, T - tb);
     const int this_buf = buf;
     advance(cur);
     buf = buf + 1 == S::kStages ? 0 : buf + 1;
@@ -230,6 +239,14 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
         for (int q = 0; q < 2; ++q)
 #pragma unroll
           for (int e = 0; e < 4; ++e) acc[i][q][e] = 0.0f;
+      if constexpr (FUSED) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) qf[m][q][e] = 0.0f;
+      }
     }
 
     // ---------------- products on the tensor cores ------------------------
@@ -272,6 +289,16 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
 #pragma unroll
             for (int n = m; n < 4; ++n)
               mma2_round2(acc[wide_gtile(m, n)], al[m], ah[n][0], ah[n][2]);
+          if constexpr (FUSED) {  // q0 of symbols 0-7 from the same fragments
+            const float2 ya = *reinterpret_cast<const float2*>(bp + box * S::kBoxBytes + yoff[kk]);
+            uint32_t bh0, bl0, bh1, bl1;
+            split_tf32(ya.x, bh0, bl0);
+            split_tf32(ya.y, bh1, bl1);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) mma2_round1(qf[m], ah[m], bh0, bh1, bl0, bl1);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) mma2_round2(qf[m], al[m], bh0, bh1);
+          }
         }
       }
     } else {
@@ -339,7 +366,18 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
         sg[wide_gim(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
-      continue;
+      if constexpr (!FUSED) {
+        continue;
+      } else {
+        // the q0 tiles of symbols 0-7 take the slots the epilogue below
+        // reads (tiles 2m; tiles 2m + 1 only reach symbols >= T)
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[2 * m][q][e] = qf[m][q][e];
+      }
     }
 
     // ---------------- q0 epilogue, sweeps, outputs ------------------------
@@ -544,11 +582,16 @@ ocd_projected_wide_kernel(const __grid_constant__ DetectParams P,
   }
   __syncwarp();
   uint32_t parity = 0;
-  wide_walk(P, &ymap, ws, bar0, parity, gw, P.Nsc, gridDim.x);
+  if (OCD_WIDE_FUSE && P.T <= 8)
+    wide_walk<true>(P, &ymap, ws, bar0, parity, gw, P.Nsc, gridDim.x);
+  else
+    wide_walk<false>(P, &ymap, ws, bar0, parity, gw, P.Nsc, gridDim.x);
 }
 
 // Several problems: each warp draws tickets (runs of subcarriers of one
 // cell) from a device counter, as ocd_batched_tma_kernel.
+// FUSED: every cell of the launch has T <= 8 (the planner groups cells by it).
+template <bool FUSED>
 __global__ void __launch_bounds__(32, OCD_WIDE_MIN_CTAS)
 ocd_batched_wide_kernel(const __grid_constant__ BatchTable tab, unsigned int* __restrict__ tickets) {
   using S = WideShape;
@@ -582,7 +625,7 @@ ocd_batched_wide_kernel(const __grid_constant__ BatchTable tab, unsigned int* __
     const long long t0 = c ? tab.cell[c - 1].tick_end : 0;
     const long long lo = ((long long)tk - t0) * C.sc_per_tick;
     const long long hi = min(lo + (long long)C.sc_per_tick, (long long)C.P.Nsc);
-    if (!wide_walk(C.P, &C.ymap, ws, bar0, parity, lo, hi, 1)) return;
+    if (!wide_walk<FUSED>(C.P, &C.ymap, ws, bar0, parity, lo, hi, 1)) return;
   }
 }
 

@@ -232,6 +232,16 @@ def test_projected_four_user_tiles(mode, U):
     check(5, 100, U, 20, 4, mode, 64, 18.0, 600 + U, label=f"100x{U}", algos=["projected"])
 
 
+@pytest.mark.parametrize("T", [1, 2, 5, 7, 8, 9])
+@pytest.mark.parametrize("B,U", [(34, 17), (130, 32), (2, 24)])
+@pytest.mark.parametrize("mode", [orc.MMSE, orc.BOX])
+def test_projected_wide_up_to_eight_symbols(mode, B, U, T):
+    """17..32 users with T <= 8 (q0 accumulated in the G phase, no q0 pass)
+    and T = 9 (one q0 pass), ragged antenna blocks."""
+    check(7, B, U, T, 3, mode, 64, 16.0, 700 + B + U + T, label=f"{B}x{U} T{T}",
+          algos=["projected"])
+
+
 @pytest.mark.parametrize("B,U,T", [(256, 32, 14), (256, 32, 1), (512, 32, 2), (34, 18, 17),
                                    (64, 32, 16), (2, 17, 3)])
 def test_projected_wide_shapes(B, U, T):
