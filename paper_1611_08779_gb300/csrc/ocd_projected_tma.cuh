@@ -49,6 +49,9 @@ namespace ocd {
 #ifndef OCD_TMA_WARPS
 #define OCD_TMA_WARPS 4       // warps per CTA
 #endif
+#ifndef OCD_TMA_SKIP_N1
+#define OCD_TMA_SKIP_N1 1     // passes of <= 8 symbols skip the second n-tile
+#endif
 #ifndef OCD_TMA_PARTS
 #define OCD_TMA_PARTS 3       // accumulator parts per tile: 3 (hh, hl, lh) or 2 (hh, hl + lh)
 #endif
@@ -251,7 +254,11 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
     // One k-step: this lane's channel entries h[m] (user m*8 + gq) and the two
     // received values.
     const bool mask_u = U < NU;  // last user tile only partly used
-    auto kstep = [&](const float2 (&h)[UT], const float2 ya, const float2 yc, auto with_g) {
+    // two_n: the pass has more than 8 symbols, so the second n-tile of
+    // received rows (symbols 8-15) is multiplied too
+    auto kstep = [&](const float2 (&h)[UT], const float2 ya, const float2 yc, auto with_g,
+                     auto two_n) {
+      constexpr bool TWO_N = decltype(two_n)::value;
       uint32_t ah[UT][3], al[UT][3];
 #pragma unroll
       for (int m = 0; m < UT; ++m) {
@@ -260,16 +267,18 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         ah[m][1] = ah[m][2] ^ 0x80000000u;       // a1 = -Im h
         al[m][1] = al[m][2] ^ 0x80000000u;
       }
-      uint32_t bh0, bl0, bh1, bl1, ch0, cl0, ch1, cl1;
+      uint32_t bh0, bl0, bh1, bl1, ch0 = 0, cl0 = 0, ch1 = 0, cl1 = 0;
       split_tf32(ya.x, bh0, bl0);
       split_tf32(ya.y, bh1, bl1);
-      split_tf32(yc.x, ch0, cl0);
-      split_tf32(yc.y, ch1, cl1);
+      if constexpr (TWO_N) {
+        split_tf32(yc.x, ch0, cl0);
+        split_tf32(yc.y, ch1, cl1);
+      }
       if constexpr (NQ == 3) {
 #pragma unroll
         for (int m = 0; m < UT; ++m) {
           mma3_tf32(qacc[m][0], ah[m], al[m], bh0, bh1, bl0, bl1);
-          mma3_tf32(qacc[m][1], ah[m], al[m], ch0, ch1, cl0, cl1);
+          if constexpr (TWO_N) mma3_tf32(qacc[m][1], ah[m], al[m], ch0, ch1, cl0, cl1);
           // G tile (m, n), n >= m: the B column j = n*8 + gq is h_j, i.e. this
           // lane's A entries of user tile n (b0 = Re, b1 = Im).
           if (decltype(with_g)::value) {
@@ -285,8 +294,10 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         for (int m = 0; m < UT; ++m) {
           mma_tf32(qacc[m][0][0], ah[m][0], ah[m][1], ah[m][2], bh0, bh1);
           mma_tf32(qacc[m][0][1], ah[m][0], ah[m][1], ah[m][2], bl0, bl1);
-          mma_tf32(qacc[m][1][0], ah[m][0], ah[m][1], ah[m][2], ch0, ch1);
-          mma_tf32(qacc[m][1][1], ah[m][0], ah[m][1], ah[m][2], cl0, cl1);
+          if constexpr (TWO_N) {
+            mma_tf32(qacc[m][1][0], ah[m][0], ah[m][1], ah[m][2], ch0, ch1);
+            mma_tf32(qacc[m][1][1], ah[m][0], ah[m][1], ah[m][2], cl0, cl1);
+          }
           if (decltype(with_g)::value) {
 #pragma unroll
             for (int n = m; n < UT; ++n) {
@@ -298,7 +309,7 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
 #pragma unroll
         for (int m = 0; m < UT; ++m) {
           mma_tf32(qacc[m][0][1], al[m][0], al[m][1], al[m][2], bh0, bh1);
-          mma_tf32(qacc[m][1][1], al[m][0], al[m][1], al[m][2], ch0, ch1);
+          if constexpr (TWO_N) mma_tf32(qacc[m][1][1], al[m][0], al[m][1], al[m][2], ch0, ch1);
           if (decltype(with_g)::value) {
 #pragma unroll
             for (int n = m; n < UT; ++n)
@@ -308,7 +319,8 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
       }
     };
     const float2* hl = sH + ta * U + gq;  // lane's channel entry, antenna offset ta
-    auto block = [&](auto with_g) {
+    auto block = [&](auto with_g, auto two_n) {
+      constexpr bool TWO_N = decltype(two_n)::value;
       if (bb == BB && !mask_u) {
         // full block, full user tiles: no masking
         for (int box = 0; box < S::kBoxes; ++box) {
@@ -319,8 +331,9 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
 #pragma unroll
             for (int m = 0; m < UT; ++m) h[m] = hl[(box * S::kBoxAnt + 2 * kk) * U + m * 8];
             const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
-            const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
-            kstep(h, ya, yc, with_g);
+            const float2 yc = TWO_N ? *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128)
+                                    : make_float2(0.f, 0.f);
+            kstep(h, ya, yc, with_g, two_n);
           }
         }
         return;
@@ -340,13 +353,21 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
             h[m] = okm ? hl[(box * S::kBoxAnt + 2 * kk) * U + m * 8] : make_float2(0.f, 0.f);
           }
           const float2 ya = *reinterpret_cast<const float2*>(yb + yoff[kk]);
-          const float2 yc = *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128);
-          kstep(h, ya, yc, with_g);
+          const float2 yc = TWO_N ? *reinterpret_cast<const float2*>(yb + yoff[kk] + 8 * 128)
+                                  : make_float2(0.f, 0.f);
+          kstep(h, ya, yc, with_g, two_n);
         }
       }
     };
-    if (first) block(std::true_type{});
-    else block(std::false_type{});
+    // passes of at most 8 symbols (T <= 8, or a short last pass) skip the
+    // second n-tile's MMAs
+    if (!OCD_TMA_SKIP_N1 || np > 8) {
+      if (first) block(std::true_type{}, std::true_type{});
+      else block(std::false_type{}, std::true_type{});
+    } else {
+      if (first) block(std::true_type{}, std::false_type{});
+      else block(std::false_type{}, std::false_type{});
+    }
     __syncwarp();
     if (blk != nblk - 1) continue;
 
