@@ -5,21 +5,24 @@
 // one subcarrier split into phases so that one warp's accumulators stay
 // within the register file:
 //
-//   G phase  (one step per 32-antenna block): only the channel block is
-//            staged; the 10 tiles (m, n), n >= m, of G are accumulated.  At
-//            the last block G goes to shared memory (Hermitian fill) with the
-//            preprocessing of Algorithm 1.
+//   G phase  (one step per staged antenna block): only the channel block
+//            is staged; the 10 tiles (m, n), n >= m, of G are accumulated.
+//            At the last block G goes to shared memory (Hermitian fill) with
+//            the preprocessing of Algorithm 1.
 //   q0 pass p (one step per block, per 16 symbols): channel block and the
 //            received rows; the 8 tiles of q0 (4 user tiles x 2 symbol
 //            tiles) are accumulated in the same registers; at the last block
 //            the K sweeps run on q and the outputs are written.
+//   T <= 8:  no q0 pass; the G phase stages the received rows too and
+//            accumulates the 4 q0 tiles of symbols 0-7 in 32 more registers
+//            from the same split channel fragments (wide_walk<true>).
 //
 // Each accumulator tile keeps two parts, hi*hi and hi*lo + lo*hi of the
 // three-term TF32 split, summed once per phase.  One warp per CTA (the
 // per-warp staging, G and preprocessing areas take 21 KB of shared memory
 // with 16-antenna blocks; q0 reuses the staging buffer of the step being
-// finished); the channel block is read once per phase, the second time
-// from L2.
+// finished); with T > 8 the channel block is read once per phase, the
+// second time from L2.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (type only; no driver library is linked)
