@@ -82,6 +82,14 @@ struct TmaShape {
   static_assert(kBufBytes % 1024 == 0, "swizzled boxes need 1024-byte alignment");
 };
 
+// G in shared memory, row i as [Re G_i0 .. Re G_i(NU-1) | Im G_i0 .. Im G_i(NU-1)]:
+// a sweep lane reads the real and the imaginary parts of its users as
+// separate 16-byte aligned runs.
+template <int NU>
+__device__ __forceinline__ int tma_gre(int i, int j) { return i * 2 * NU + j; }
+template <int NU>
+__device__ __forceinline__ int tma_gim(int i, int j) { return i * 2 * NU + NU + j; }
+
 // Fault word of the bulk-copy kernels (bit 0: a wait timed out).  Defined
 // here because exactly one translation unit (ocd_projected_tma.cu) includes
 // this header; the host reads it through projected_tma_fault().
@@ -399,11 +407,11 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
             const float re = (a[NQ - 1][e] + (NQ == 3 ? a[1][e] : 0.0f)) + a[0][e];
             const float im = (a[NQ - 1][2 + e] + (NQ == 3 ? a[1][2 + e] : 0.0f)) + a[0][2 + e];
             const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
-            sg[2 * (i * NU + j)] = re;
-            sg[2 * (i * NU + j) + 1] = im;
+            sg[tma_gre<NU>(i, j)] = re;
+            sg[tma_gim<NU>(i, j)] = im;
             if (n != m) {  // lower block from Hermitian symmetry
-              sg[2 * (j * NU + i)] = re;
-              sg[2 * (j * NU + i) + 1] = -im;
+              sg[tma_gre<NU>(j, i)] = re;
+              sg[tma_gim<NU>(j, i)] = -im;
             }
           }
     }
@@ -411,7 +419,7 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
     // (2) preprocessing (Algorithm 1) and soft-output constants
     if (first) {
       if (lane < NU) {
-        const float nrm = sg[2 * (lane * NU + lane)];
+        const float nrm = sg[tma_gre<NU>(lane, lane)];
         const float den = nrm + P.alpha;
         const float dinv = (lane < U && den > 0.0f) ? 1.0f / den : 0.0f;
         const float p = dinv * nrm;
@@ -419,7 +427,7 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         spre[4 * lane + 1] = p;
         spre[4 * lane + 2] = nrm;
         spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
-        sg[2 * (lane * NU + lane) + 1] = 0.0f;  // G_uu is real
+        sg[tma_gim<NU>(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
     }
@@ -465,15 +473,18 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
             const float dr = __shfl_sync(kFullMask, dr0, owner);
             const float di = __shfl_sync(kFullMask, di0, owner);
             // q <- q - G[:, u] dz for my users, with G[j][u] = conj(G[u][j])
-            const float4* gu = reinterpret_cast<const float4*>(sg + 2 * (u * NU + hf * UP));
+            const float4* gre = reinterpret_cast<const float4*>(sg + tma_gre<NU>(u, hf * UP));
+            const float4* gim = reinterpret_cast<const float4*>(sg + tma_gim<NU>(u, hf * UP));
 #pragma unroll
-            for (int l2 = 0; l2 < UP / 2; ++l2) {
-              const float4 g2 = gu[l2];
-              const int l = 2 * l2;
-              qr[l] = fmaf(-g2.x, dr, fmaf(-g2.y, di, qr[l]));
-              qi[l] = fmaf(-g2.x, di, fmaf(g2.y, dr, qi[l]));
-              qr[l + 1] = fmaf(-g2.z, dr, fmaf(-g2.w, di, qr[l + 1]));
-              qi[l + 1] = fmaf(-g2.z, di, fmaf(g2.w, dr, qi[l + 1]));
+            for (int l4 = 0; l4 < UP / 4; ++l4) {
+              const float4 r4 = gre[l4], i4 = gim[l4];
+              const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int l = 4 * l4 + c;
+                qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
+                qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
+              }
             }
           }
         }

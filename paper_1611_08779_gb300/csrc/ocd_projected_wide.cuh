@@ -31,6 +31,7 @@
 
 #include "ocd_batch.cuh"
 #include "ocd_common.cuh"
+#include "ocd_f32x2.cuh"
 #include "ocd_mma.cuh"
 #include "ocd_tma_util.cuh"
 
@@ -84,20 +85,6 @@ __device__ __forceinline__ int wide_gre(int i, int j) { return i * 2 * WideShape
 __device__ __forceinline__ int wide_gim(int i, int j) {
   return i * 2 * WideShape::kUsers + WideShape::kUsers + j;
 }
-// Packed FP32 pairs (fma.rn.f32x2: two independent IEEE fmas).
-__device__ __forceinline__ unsigned long long wide_pack2(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void wide_unpack2(unsigned long long v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ void wide_fma2(unsigned long long& d, unsigned long long a,
-                                          unsigned long long b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-
 // Fault word of the wide kernels (bit 0: a wait timed out; bit 1: a batched
 // cell's tensor map was misaligned).  Defined here because exactly one
 // translation unit (ocd_projected_wide.cu) includes this header.
@@ -413,8 +400,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
 #pragma unroll
       for (int l2 = 0; l2 < UP / 2; ++l2) {
         const int j = hf * UP + 2 * l2;
-        QR[l2] = act ? wide_pack2(sq[2 * (ts * NU + j)], sq[2 * (ts * NU + j + 1)]) : 0ull;
-        QI[l2] = act ? wide_pack2(sq[2 * (ts * NU + j) + 1], sq[2 * (ts * NU + j + 1) + 1]) : 0ull;
+        QR[l2] = act ? f2_pack(sq[2 * (ts * NU + j)], sq[2 * (ts * NU + j + 1)]) : 0ull;
+        QI[l2] = act ? f2_pack(sq[2 * (ts * NU + j) + 1], sq[2 * (ts * NU + j + 1) + 1]) : 0ull;
         zr[2 * l2] = zr[2 * l2 + 1] = 0.0f;
         zi[2 * l2] = zi[2 * l2 + 1] = 0.0f;
       }
@@ -429,8 +416,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
           if (u < U) {
             const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
             float q0, q1, p0, p1;
-            wide_unpack2(QR[lu >> 1], q0, q1);
-            wide_unpack2(QI[lu >> 1], p0, p1);
+            f2_unpack(QR[lu >> 1], q0, q1);
+            f2_unpack(QI[lu >> 1], p0, p1);
             const float qr = (lu & 1) ? q1 : q0;
             const float qi = (lu & 1) ? p1 : p0;
             float wr = fmaf(dp.x, qr, dp.y * zr[lu]);
@@ -443,25 +430,25 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
             const int owner = (lane & ~1) | oh;
             const float dr = __shfl_sync(kFullMask, dr0, owner);
             const float di = __shfl_sync(kFullMask, di0, owner);
-            const unsigned long long DR = wide_pack2(dr, dr);
-            const unsigned long long NDR = wide_pack2(-dr, -dr);
-            const unsigned long long NDI = wide_pack2(-di, -di);
+            const unsigned long long DR = f2_pack(dr, dr);
+            const unsigned long long NDR = f2_pack(-dr, -dr);
+            const unsigned long long NDI = f2_pack(-di, -di);
             const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
             const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
 #pragma unroll
             for (int l4 = 0; l4 < UP / 4; ++l4) {
               const float4 r4 = gre[l4], i4 = gim[l4];
-              const unsigned long long re0 = wide_pack2(r4.x, r4.y), re1 = wide_pack2(r4.z, r4.w);
-              const unsigned long long im0 = wide_pack2(i4.x, i4.y), im1 = wide_pack2(i4.z, i4.w);
+              const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
+              const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
               // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
-              wide_fma2(QR[2 * l4], im0, NDI);
-              wide_fma2(QR[2 * l4], re0, NDR);
-              wide_fma2(QI[2 * l4], im0, DR);
-              wide_fma2(QI[2 * l4], re0, NDI);
-              wide_fma2(QR[2 * l4 + 1], im1, NDI);
-              wide_fma2(QR[2 * l4 + 1], re1, NDR);
-              wide_fma2(QI[2 * l4 + 1], im1, DR);
-              wide_fma2(QI[2 * l4 + 1], re1, NDI);
+              f2_fma(QR[2 * l4], im0, NDI);
+              f2_fma(QR[2 * l4], re0, NDR);
+              f2_fma(QI[2 * l4], im0, DR);
+              f2_fma(QI[2 * l4], re0, NDI);
+              f2_fma(QR[2 * l4 + 1], im1, NDI);
+              f2_fma(QR[2 * l4 + 1], re1, NDR);
+              f2_fma(QI[2 * l4 + 1], im1, DR);
+              f2_fma(QI[2 * l4 + 1], re1, NDI);
             }
           }
         }
