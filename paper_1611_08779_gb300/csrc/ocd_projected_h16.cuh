@@ -54,6 +54,14 @@ struct H16Shape {
   static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
 };
 
+// G in shared memory, row i as [Re G_i0 .. Re G_i(NU-1) | Im G_i0 .. Im G_i(NU-1)]:
+// a sweep lane reads the real and the imaginary parts of its users as
+// separate 16-byte aligned runs.
+template <int NU>
+__device__ __forceinline__ int h16_gre(int i, int j) { return i * 2 * NU + j; }
+template <int NU>
+__device__ __forceinline__ int h16_gim(int i, int j) { return i * 2 * NU + NU + j; }
+
 // D += A B for one m16n8k16 tile with 16-bit inputs and FP32 accumulation.
 template <int STORE>
 __device__ __forceinline__ void mma16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
@@ -271,18 +279,18 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
           for (int e = 0; e < 2; ++e) {
             const float* d = gacc[m == 0 ? n : 2];
             const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
-            sg[2 * (i * NU + j)] = d[e];
-            sg[2 * (i * NU + j) + 1] = d[2 + e];
+            sg[h16_gre<NU>(i, j)] = d[e];
+            sg[h16_gim<NU>(i, j)] = d[2 + e];
             if (n != m) {  // lower block from Hermitian symmetry
-              sg[2 * (j * NU + i)] = d[e];
-              sg[2 * (j * NU + i) + 1] = -d[2 + e];
+              sg[h16_gre<NU>(j, i)] = d[e];
+              sg[h16_gim<NU>(j, i)] = -d[2 + e];
             }
           }
     }
     __syncwarp();
     if (first) {
       if (lane < NU) {
-        const float nrm = sg[2 * (lane * NU + lane)];
+        const float nrm = sg[h16_gre<NU>(lane, lane)];
         const float den = nrm + P.alpha;
         const float dinv = (lane < U && den > 0.0f) ? 1.0f / den : 0.0f;
         const float p = dinv * nrm;
@@ -290,7 +298,7 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
         spre[4 * lane + 1] = p;
         spre[4 * lane + 2] = nrm;
         spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
-        sg[2 * (lane * NU + lane) + 1] = 0.0f;  // G_uu is real
+        sg[h16_gim<NU>(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
     }
@@ -331,15 +339,18 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
             const int owner = (lane & ~1) | oh;
             const float dr = __shfl_sync(kFullMask, dr0, owner);
             const float di = __shfl_sync(kFullMask, di0, owner);
-            const float4* gu = reinterpret_cast<const float4*>(sg + 2 * (u * NU + hf * UP));
+            const float4* gre = reinterpret_cast<const float4*>(sg + h16_gre<NU>(u, hf * UP));
+            const float4* gim = reinterpret_cast<const float4*>(sg + h16_gim<NU>(u, hf * UP));
 #pragma unroll
-            for (int l2 = 0; l2 < UP / 2; ++l2) {
-              const float4 g2 = gu[l2];
-              const int l = 2 * l2;
-              qr[l] = fmaf(-g2.x, dr, fmaf(-g2.y, di, qr[l]));
-              qi[l] = fmaf(-g2.x, di, fmaf(g2.y, dr, qi[l]));
-              qr[l + 1] = fmaf(-g2.z, dr, fmaf(-g2.w, di, qr[l + 1]));
-              qi[l + 1] = fmaf(-g2.z, di, fmaf(g2.w, dr, qi[l + 1]));
+            for (int l4 = 0; l4 < UP / 4; ++l4) {
+              const float4 r4 = gre[l4], i4 = gim[l4];
+              const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int l = 4 * l4 + c;
+                qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
+                qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
+              }
             }
           }
         }
