@@ -858,7 +858,7 @@ def run_unfolded(args):
     return 0
 
 
-def main(argv=None):
+def parser():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -882,6 +882,11 @@ def main(argv=None):
     ap.add_argument("--cells", type=int, default=24, help="cells of the batched workload")
     ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
                     help="seconds of clock sampling the timed steps are extended to")
+    return ap
+
+
+def main(argv=None):
+    ap = parser()
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

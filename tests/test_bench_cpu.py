@@ -76,3 +76,26 @@ def test_cpu_baseline_line_reports_all_oracle_forms():
     assert line["kind"] == "oracle" and line["unit"] == "Gb/s" and line["value"] > 0
     assert line["single_core"]["value"] > 0 and line["numpy_oracle"]["value"] > 0
     assert line["cores"] >= 1
+
+
+def test_recorded_traffic_matches_the_current_kernel_sources():
+    """The committed ncu summary of the dominant kernel was taken on the
+    sources that are built now (else the bench reports traffic null)."""
+    assert bench.recorded_traffic() is not None, (
+        "kernel sources changed since the committed profile: retake the ncu capture")
+
+
+def test_commands_in_profiles_parse():
+    """Every bench.py command line quoted in profiles/ is valid for the
+    current argument parser."""
+    import glob
+    import shlex
+    found = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            if "python bench.py" not in line:
+                continue
+            argv = shlex.split(line.split("python bench.py", 1)[1].strip())
+            bench.parser().parse_args(argv)
+            found += 1
+    assert found >= 4
