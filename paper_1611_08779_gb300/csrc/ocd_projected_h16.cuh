@@ -366,23 +366,36 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       }
       __syncwarp();
     }
-    for (int f = lane; f < np * U; f += 32) {
-      const int ts = f / U;
-      const int u = f - ts * U;
-      const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
-      const long long o = (sc * T + tb + ts) * U + u;
-      if (P.xhat) P.xhat[o] = z;
-      if (P.llr) {
-        float* out = P.llr + o * P.Q;
-        const float inv = spre[4 * u + 3];
-        if (!(inv > 0.0f)) {
-          for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
-        } else {
-          const float rho = spre[4 * u + 2] * P.rho_scale;
-          dimension_llr(z.x * inv, rho, P, out);
-          if (!P.bpsk) dimension_llr(z.y * inv, rho, P, out + P.nb);
+    // outputs: a full user tile splits the item index with a shift instead
+    // of a division by U; the LLR code is chosen once per pass by the bits
+    // per real dimension
+    auto outputs = [&](auto nbc) {
+      constexpr int NB = decltype(nbc)::value;
+      const bool full_tile = U == NU;
+      for (int f = lane; f < np * U; f += 32) {
+        const int ts = full_tile ? f / NU : f / U;
+        const int u = f - ts * U;
+        const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
+        const long long o = (sc * T + tb + ts) * U + u;
+        if (P.xhat) P.xhat[o] = z;
+        if (P.llr) {
+          float* out = P.llr + o * P.Q;
+          const float inv = spre[4 * u + 3];
+          if (!(inv > 0.0f)) {
+            for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
+          } else {
+            const float rho = spre[4 * u + 2] * P.rho_scale;
+            dimension_llr_nb<NB>(z.x * inv, rho, P.lvl_step, out);
+            if (!P.bpsk) dimension_llr_nb<NB>(z.y * inv, rho, P.lvl_step, out + NB);
+          }
         }
       }
+    };
+    switch (P.nb) {
+      case 1: outputs(std::integral_constant<int, 1>{}); break;
+      case 2: outputs(std::integral_constant<int, 2>{}); break;
+      case 3: outputs(std::integral_constant<int, 3>{}); break;
+      default: outputs(std::integral_constant<int, 4>{}); break;
     }
     __syncwarp();
   }
