@@ -1,7 +1,9 @@
 """Unfolded (differentiable) OCD on the GPU: forward values against the FP64
 reference of oracle/unfolded.py, gradients of the BCE loss with respect to
-the per-sweep damping and regularizer against FP64 autograd and against
-finite differences of the GPU forward, and the edge cases of the adjoint."""
+the per-sweep damping and regularizer -- each component on its own --
+against FP64 autograd, against central differences of the FP64 forward and
+of the GPU forward, at small sizes and at the 4096-sample training batch,
+and the edge cases of the adjoint."""
 import math
 
 import numpy as np
@@ -65,6 +67,30 @@ def gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t, arr="auto"):
 
 ARR = ["residual", "projected"]
 
+# Element-wise bound on each gradient component, applied to the omega family
+# and to the alpha family separately (the alpha gradients are typically an
+# order of magnitude smaller than the omega gradients, so one bound over the
+# joined vector would not constrain them):
+#     |g_k - g_ref,k| <= GRAD_RTOL * max(|g_ref,k|, GRAD_FLOOR * max_j |g_ref,j|)
+# with max_j over the same family.  The GPU forward carries about 1e-6
+# relative rounding error per value (FP32, TF32 split products); the adjoint
+# replays it and sums per-sample partials in FP32, so a component is good to
+# about 1e-5 of the family's scale.  The floor keeps a component that cancels
+# to nearly zero from demanding a relative accuracy FP32 cannot give it.
+GRAD_RTOL = 2e-3
+GRAD_FLOOR = 1e-2
+
+
+def assert_grad_close(g, g_ref, name):
+    g = np.asarray(g, dtype=np.float64)
+    g_ref = np.asarray(g_ref, dtype=np.float64)
+    floor = GRAD_FLOOR * float(np.max(np.abs(g_ref)))
+    bound = GRAD_RTOL * np.maximum(np.abs(g_ref), floor) + 1e-12
+    err = np.abs(g - g_ref)
+    assert np.all(err <= bound), (
+        f"{name}: per-component error / bound = {np.array2string(err / bound, precision=3)}; "
+        f"gpu {g}, fp64 {g_ref}")
+
 
 @pytest.mark.parametrize("arr", ARR)
 @pytest.mark.parametrize("mode", ["box", "mmse"])
@@ -98,14 +124,51 @@ def test_gradients_match_fp64_autograd(mode, B, U, T, K, order, arr):
     bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
     loss, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t, arr)
     assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
-    g = np.concatenate([gom, gal])
-    g_ref = np.concatenate([gom_ref, gal_ref])
-    assert np.linalg.norm(g - g_ref) <= 2e-3 * np.linalg.norm(g_ref) + 1e-6, (g, g_ref)
+    assert_grad_close(gom, gom_ref, "d loss / d omega")
+    assert_grad_close(gal, gal_ref, "d loss / d alpha")
+
+
+@pytest.mark.parametrize("arr", ARR)
+def test_gradient_matches_finite_differences_of_the_fp64_forward(arr):
+    """Each omega_k and alpha_k gradient of the GPU adjoint against central
+    differences of the FP64 forward (step 1e-6: truncation and rounding of
+    the difference are both below 1e-8 of the gradient, and a step that small
+    crosses no kink of the box or of the max-log minima in practice).  This
+    checks the adjoint without going through the reference's autograd."""
+    H, Y, N0, bits = problem(96, 64, 8, 2, 16, seed=31)
+    om, al = params(4, seed=3)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    _, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, arr)
+    H64, Y64, N064 = H.astype(np.complex128), Y.astype(np.complex128), N0.astype(np.float64)
+
+    def f(o, a):
+        with torch.no_grad():
+            _, llr = orc.unfolded_forward(H64, Y64, N064, 1.0, torch.as_tensor(o),
+                                          torch.as_tensor(a), orc.BOX, 16)
+            return float(orc.bce_loss(llr, bits))
+
+    eps = 1e-6
+    om64, al64 = om.astype(np.float64), al.astype(np.float64)
+    fd_o, fd_a = np.zeros(4), np.zeros(4)
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = eps
+        fd_o[k] = (f(om64 + e, al64) - f(om64 - e, al64)) / (2 * eps)
+        fd_a[k] = (f(om64, al64 + e) - f(om64, al64 - e)) / (2 * eps)
+    assert_grad_close(gom, fd_o, "d loss / d omega vs FP64 differences")
+    assert_grad_close(gal, fd_a, "d loss / d alpha vs FP64 differences")
 
 
 @pytest.mark.parametrize("arr", ARR)
 def test_gradient_matches_finite_differences_of_the_gpu_forward(arr):
-    H, Y, N0, bits = problem(64, 64, 8, 2, 16, seed=31)
+    """The GPU adjoint against central differences of the GPU forward itself
+    (both FP32): a consistency check of the two kernels.  The difference of
+    two FP32 losses carries rounding noise of about 1e-7 of the loss, i.e.
+    about 2e-5 absolute over a step of 2e-3 at this size (1024 samples x 8
+    users x 4 bits), so each component is held to 2% of itself with an
+    absolute floor of 5e-4: an alpha gradient of 1e-3 is bounded to +-2e-5."""
+    H, Y, N0, bits = problem(512, 64, 8, 2, 16, seed=31)
     om, al = params(4, seed=3)
     Hd, Yd, N0d = to_dev(H, Y, N0)
     bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
@@ -123,8 +186,25 @@ def test_gradient_matches_finite_differences_of_the_gpu_forward(arr):
         e[k] = eps
         fd_o = (f(om + e, al) - f(om - e, al)) / (2 * eps)
         fd_a = (f(om, al + e) - f(om, al - e)) / (2 * eps)
-        assert abs(fd_o - gom[k]) <= 3e-2 * max(abs(fd_o), 1e-2), (k, fd_o, gom[k])
-        assert abs(fd_a - gal[k]) <= 3e-2 * max(abs(fd_a), 1e-2), (k, fd_a, gal[k])
+        assert abs(fd_o - gom[k]) <= 2e-2 * max(abs(fd_o), 5e-4), (k, fd_o, gom[k])
+        assert abs(fd_a - gal[k]) <= 2e-2 * max(abs(fd_a), 5e-4), (k, fd_a, gal[k])
+
+
+@pytest.mark.parametrize("arr", ARR)
+def test_gradients_at_the_training_batch_size(arr):
+    """The unfolded benchmark's configuration: 4096 (subcarrier, symbol)
+    samples of 128x16, K = 5, 16-QAM, SNR uniform in 5-25 dB, OCD-BOX, BCE
+    loss; same launch partition and gradient reduction as the benchmark
+    step.  Every omega_k and alpha_k against FP64 autograd."""
+    H, Y, N0, bits = problem(4096, 128, 16, 1, 16, seed=21)
+    om, al = params(5, seed=9)
+    loss_ref, gom_ref, gal_ref = reference(H, Y, N0, om, al, "box", 16, bits)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    loss, gom, gal = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, arr)
+    assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
+    assert_grad_close(gom, gom_ref, "d loss / d omega")
+    assert_grad_close(gal, gal_ref, "d loss / d alpha")
 
 
 def test_gradient_through_xhat_only():
@@ -142,9 +222,8 @@ def test_gradient_through_xhat_only():
     z, _ = orc.unfolded_forward(H.astype(np.complex128), Y.astype(np.complex128), N0.astype(np.float64),
                                 1.0, om64, al64, orc.BOX, 16)
     (z * torch.as_tensor(c)).real.sum().backward()
-    g = np.concatenate([o.grad.cpu().numpy(), a.grad.cpu().numpy()])
-    g_ref = np.concatenate([om64.grad.numpy(), al64.grad.numpy()])
-    assert np.linalg.norm(g - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
+    assert_grad_close(o.grad.cpu().numpy(), om64.grad.numpy(), "d <c, xhat> / d omega")
+    assert_grad_close(a.grad.cpu().numpy(), al64.grad.numpy(), "d <c, xhat> / d alpha")
 
 
 @pytest.mark.parametrize("arr", ARR)
@@ -168,9 +247,8 @@ def test_arrangements_agree():
     res = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, "residual")
     prj = gpu_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, "projected")
     assert abs(res[0] - prj[0]) <= 1e-5 * abs(res[0])
-    g1 = np.concatenate(res[1:])
-    g2 = np.concatenate(prj[1:])
-    assert np.linalg.norm(g1 - g2) <= 2e-3 * np.linalg.norm(g1)
+    assert_grad_close(prj[1], res[1], "d loss / d omega, projected vs residual")
+    assert_grad_close(prj[2], res[2], "d loss / d alpha, projected vs residual")
 
 
 def test_projected_rejects_a_channel_copy_that_does_not_fit():
