@@ -213,11 +213,9 @@ def cpu_baseline_line(args):
     r2, el2, _ = cpu_oracle_rate(d2, args.cpu_seconds / 4, args.mode, impl="numpy")
     return {
         "value": r, "unit": "Gb/s", "cores": oracle_threads(), "kind": "oracle",
-        "sample": f"{NSC_FRAME} subcarriers x {T} symbols of the same workload, detected "
-                  f"{done // NSC_FRAME} times ({el:.1f} s of the FP64 C oracle, one subcarrier "
-                  f"per OpenMP iteration, on all host cores)",
-        "single_core": {"value": r1, "unit": "Gb/s", "seconds": el1},
-        "numpy_oracle": {"value": r2, "unit": "Gb/s", "cores": 1, "seconds": el2},
+        "sample": f"{NSC_FRAME} subcarriers x {T} symbols of the workload, {done // NSC_FRAME} "
+                  f"times in {el:.1f} s (FP64 C oracle, all host cores)",
+        "single_core_gbps": _r(r1), "numpy_oracle_gbps": _r(r2),
     }
 
 
@@ -272,19 +270,33 @@ def workload_config(args, nsc):
             "l2": "inputs larger than L2 (no flush)", "parallelism": f"subcarriers x{args.gpus}"}
 
 
-def form_summary(measure, args, keys):
+def form_summary(measure, args):
     """One of the extra forms measured beside the headline number, reduced to
-    `keys`; a failure is reported in the object instead of losing the line."""
+    its compact summary; a failure is reported in the object instead of
+    losing the line."""
     import argparse as _ap
     sub = _ap.Namespace(**vars(args))
     sub.steps = min(args.steps, 50)
     try:
         res = measure(sub)
     except Exception as exc:  # reported, not hidden: the key says what failed
-        return {"error": f"{type(exc).__name__}: {exc}"}
-    out = {k: res[k] for k in keys if k in res}
-    out["metric"] = res["metric"]
-    return out
+        return {"error": f"{type(exc).__name__}: {exc}"[:200]}
+    return _r(res["summary"])
+
+
+def _r(x, digits=4):
+    """Floats of a summary rounded to `digits` significant digits (the line
+    stays short enough to be kept whole by a log tail)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if math.isfinite(x) else x
+    if isinstance(x, dict):
+        return {k: _r(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_r(v, digits) for v in x]
+    return x
+
+
+SWEEP_SNR_DB = (0.0, 15.0, 30.0)
 
 
 def run_ours(args):
@@ -308,6 +320,10 @@ def run_ours(args):
     llr = torch.empty((nsc, T, U, Q), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(dev)
     N0 = d["N0"]
+    peaks, src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    alg_bytes = algorithmic_bytes_per_sc() * nsc
+    bits_per_step = nsc * T * U * Q * world
 
     def step():
         ocd.ocd_detect(H, Y, N0, 1.0, K, args.mode, ORDER, xhat=xhat, llr=llr, stream=stream)
@@ -317,12 +333,35 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def max_over_ranks(ms):
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def timed_ms(fn, steps, warm=3):
+        """Mean device time of one fn() on `stream` (CUDA events, warm-up
+        untimed, synchronized on both sides), max over ranks."""
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                fn()
+        barrier()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(steps):
+                fn()
+            ev1.record(stream)
+        barrier()
+        return max_over_ranks(ev0.elapsed_time(ev1) / steps)
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
     barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(dev.index)
     with sampler:
         with torch.cuda.stream(stream):
@@ -341,36 +380,34 @@ def run_ours(args):
                 for _ in range(hold):
                     step()
             barrier()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    bits_per_step = nsc * T * U * Q * world
+    ms = max_over_ranks(ms)
     value = bits_per_step * args.steps / (ms / 1e3) / 1e9
+    form_steps = max(3, min(args.steps, 50))
+
+    # Both modes of Algorithm 1 over the SNR sweep of the metric configuration
+    # (same channels, bits and noise draw; only the noise scale changes), the
+    # same launch on the same stream.
+    sweep = {}
+    if not args.no_forms:
+        for snr in SWEEP_SNR_DB:
+            ds = synth.make_uplink(nsc, B, U, T, ORDER, snr, seed=7 + rank)
+            Ys = torch.from_numpy(ds["Y"]).to(dev)
+            del ds["H"], ds["Y"]
+            for mode in ("box", "mmse"):
+                msp = timed_ms(lambda: ocd.ocd_detect(H, Ys, ds["N0"], 1.0, K, mode, ORDER,
+                                                      xhat=xhat, llr=llr, stream=stream),
+                               form_steps)
+                sweep.setdefault(mode, {})[f"{snr:g}"] = [
+                    bits_per_step / world / (msp / 1e3) / 1e9,
+                    alg_bytes / (msp / 1e3) / 1e9 / hbm_peak]
+            del Ys
+        barrier()
 
     # The residual arrangement (Algorithm 1 as written, r kept in full) on the
-    # same inputs, timed the same way.
-    def step_residual():
-        ocd.ocd_detect(H, Y, N0, 1.0, K, args.mode, ORDER, xhat=xhat, llr=llr, stream=stream,
-                       algo="residual")
-
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            step_residual()
-    barrier()
-    res_steps = max(3, min(args.steps, 50))
-    ev0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(res_steps):
-            step_residual()
-    ev1.record(stream)
-    barrier()
-    ms_res = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_res], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_res = float(t.item())
-    value_res = bits_per_step * res_steps / (ms_res / 1e3) / 1e9
+    # same inputs: the plain FP32 form the metric compares against.
+    ms_res = timed_ms(lambda: ocd.ocd_detect(H, Y, N0, 1.0, K, args.mode, ORDER, xhat=xhat,
+                                             llr=llr, stream=stream, algo="residual"),
+                      form_steps)
 
     # Precision forms: the same batch with H and Y stored as bfloat16 / float16
     # pairs, timed the same way, and compared with the float32-storage outputs.
@@ -381,42 +418,38 @@ def run_ours(args):
         H16, Y16 = to16(H, dt), to16(Y, dt)
         x16 = torch.empty_like(xhat)
         l16 = torch.empty_like(llr)
-
-        def step16():
-            ocd.ocd_detect(H16, Y16, N0, 1.0, K, args.mode, ORDER, xhat=x16, llr=l16, stream=stream)
-
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                step16()
-        barrier()
-        n16 = max(3, min(args.steps, 200))
-        ev0.record(stream)
-        with torch.cuda.stream(stream):
-            for _ in range(n16):
-                step16()
-        ev1.record(stream)
-        barrier()
-        ms16 = ev0.elapsed_time(ev1) / n16
+        ms16 = timed_ms(lambda: ocd.ocd_detect(H16, Y16, N0, 1.0, K, args.mode, ORDER, xhat=x16,
+                                               llr=l16, stream=stream),
+                        max(3, min(args.steps, 200)))
         b16 = algorithmic_bytes_per_sc_stored(B, U, T, Q, 4) * nsc
         agree = float(((l16 > 0) == (lr > 0)).float().mean().item())
-        xerr = float(((x16 - xr).abs().pow(2).sum(-1).sqrt()
-                      / xr.abs().pow(2).sum(-1).sqrt().clamp_min(1e-3 * math.sqrt(U))).max().item())
-        forms[name] = {"value": bits_per_step / world / (ms16 / 1e3) / 1e9, "unit": "Gb/s",
-                       "ms_per_step": ms16,
-                       "hbm_frac": b16 / (ms16 / 1e3) / 1e9 / float(measured_peaks()[0].get(
-                           "hbm_gbs", FALLBACK_HBM_GBS)),
-                       "algorithmic_bytes_per_launch": b16,
-                       "hard_bit_agreement_vs_f32_storage": agree,
-                       "max_xhat_rel_diff_vs_f32_storage": xerr}
+        forms[name] = {"gbps": bits_per_step / world / (ms16 / 1e3) / 1e9, "ms": ms16,
+                       "hbm_frac": b16 / (ms16 / 1e3) / 1e9 / hbm_peak,
+                       "bits_equal_f32": agree}
         del H16, Y16, x16, l16
 
     # End to end through the host-buffer entry point: pinned inputs copied in
-    # and results copied out inside the timed region.
+    # and results copied out inside the timed region.  Its ceiling: the
+    # pinned copies alone (one direction at a time, same bytes, same stream),
+    # with the two directions and the kernel fully overlapped.
     Hh = torch.from_numpy(d["H"]).pin_memory()
     Yh = torch.from_numpy(d["Y"]).pin_memory()
     xh = torch.empty((nsc, T, U), dtype=torch.complex64, pin_memory=True)
     lh = torch.empty((nsc, T, U, Q), dtype=torch.float32, pin_memory=True)
     staging = {"H": H, "Y": Y, "X": xhat, "L": llr}
+    h2d_bytes = int(Hh.numel() * 8 + Yh.numel() * 8)
+    d2h_bytes = int(xh.numel() * 8 + lh.numel() * 4)
+
+    def h2d():
+        H.copy_(Hh, non_blocking=True)
+        Y.copy_(Yh, non_blocking=True)
+
+    def d2h():
+        xh.copy_(xhat, non_blocking=True)
+        lh.copy_(llr, non_blocking=True)
+
+    ms_h2d = timed_ms(h2d, 3, warm=1)
+    ms_d2h = timed_ms(d2h, 3, warm=1)
 
     def e2e_step():
         ocd.ocd_detect_host(Hh, Yh, N0, 1.0, K, args.mode, ORDER, xhat=xh, llr=lh,
@@ -431,28 +464,21 @@ def run_ours(args):
         e2e_step()
     ev1.record(stream)
     barrier()
-    ms_e2e = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ev0.elapsed_time(ev1))
     e2e_value = bits_per_step * e2e_steps / (ms_e2e / 1e3) / 1e9
+    e2e_ceiling = bits_per_step / (max(ms_h2d, ms_d2h, ms / args.steps) / 1e3) / 1e9
 
     if rank == 0:
-        peaks, src = measured_peaks()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         per_launch_s = ms / 1e3 / args.steps
-        hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-        alg_bytes = algorithmic_bytes_per_sc() * nsc
         achieved_gbs = alg_bytes / per_launch_s / 1e9
         traffic = recorded_traffic()
         clocks = sampler.summary()
         if clocks is not None:
             clocks["window"] = "timed region" if hold == 0 else \
-                f"timed region + {hold} identical untimed steps (window >= {args.clock_window} s)"
+                f"timed region + {hold} untimed identical steps"
         alu_peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-        res_launch_s = ms_res / 1e3 / res_steps
-        res_tf = 2 * algorithmic_fma_per_sc() * nsc / res_launch_s / 1e12
+        res_tf = 2 * algorithmic_fma_per_sc() * nsc / (ms_res / 1e3) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": "Gb/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -461,34 +487,32 @@ def run_ours(args):
             "config": workload_config(args, nsc),
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved_gbs / hbm_peak, "traffic": traffic,
-                         "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+                         "peak_source": f"{src} hbm_gbs",
                          "kernel": "ocd_projected_tma_kernel",
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "ceiling_gbps": hbm_peak * 1e9 / (alg_bytes / nsc) * T * U * Q / 1e9},
-            "residual_form": {
-                "value": value_res, "unit": "Gb/s", "kernel": "ocd_residual_kernel",
-                "steps": res_steps, "ms_per_step": ms_res / res_steps,
-                "roofline": {"bound": "alu", "achieved": res_tf, "peak": alu_peak,
-                             "unit": "TFLOP/s", "frac": res_tf / alu_peak,
-                             "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x "
-                                            f"{SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)"}},
-            "precision_forms": forms,
-            "e2e": {"value": e2e_value, "unit": "Gb/s",
-                    "h2d_bytes_per_step": int(Hh.numel() * 8 + Yh.numel() * 8),
-                    "d2h_bytes_per_step": int(xh.numel() * 8 + lh.numel() * 4),
-                    "pieces": args.pieces},
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "e2e": {"value": e2e_value, "unit": "Gb/s", "h2d_bytes_per_step": h2d_bytes,
+                    "d2h_bytes_per_step": d2h_bytes, "pieces": args.pieces,
+                    "h2d_gbs": h2d_bytes / (ms_h2d / 1e3) / 1e9,
+                    "d2h_gbs": d2h_bytes / (ms_d2h / 1e3) / 1e9,
+                    "ceiling_gbps": e2e_ceiling, "frac": e2e_value / e2e_ceiling},
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
-        if not args.no_forms:
-            line["batched_form"] = form_summary(measure_batched, args, (
-                "value", "unit", "ms_per_step", "arms_gbps", "roofline", "config"))
-            line["unfolded_form"] = form_summary(measure_unfolded, args, (
-                "value", "unit", "ms_per_step", "forward_ms", "roofline", "config"))
-            line["single_symbol_form"] = form_summary(measure_single, args, ("forms",))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_line(args)
-        print(json.dumps(line), flush=True)
+        # Forms measured beside the headline, last and rounded so that the
+        # line stays short: [Gb/s, fraction of the HBM roofline] per point.
+        line["snr_sweep"] = _r({"unit": "[Gb/s, hbm frac]", **sweep}) if sweep else None
+        line["residual_form"] = _r({
+            "gbps": bits_per_step / world / (ms_res / 1e3) / 1e9, "ms": ms_res,
+            "alu_frac": res_tf / alu_peak, "kernel": "ocd_residual_kernel",
+            "alu_peak_tflops": alu_peak})
+        line["precision_forms"] = _r(forms)
+        if not args.no_forms:
+            line["batched_form"] = form_summary(measure_batched, args)
+            line["unfolded_form"] = form_summary(measure_unfolded, args)
+            line["single_symbol_form"] = form_summary(measure_single, args)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -627,9 +651,12 @@ def measure_single(args):
                               "unit": "Gb/s", "ms_per_step": arms["residual"]},
         }
         del H, Y, x, llr
+    summary = {"unit": "[Gb/s, hbm frac, residual-form Gb/s]", "kernel": "ocd_projected_lane_kernel"}
+    for key, f in out.items():
+        summary[key] = [f["value"], f["roofline"]["frac"], f["residual_form"]["value"]]
     return {"metric": "detected Gb/s, one symbol per channel (T=1, K=3)", "forms": out,
             "value": out["128x8"]["value"], "unit": "Gb/s",
-            "ms_per_step": out["128x8"]["ms_per_step"]}
+            "ms_per_step": out["128x8"]["ms_per_step"], "summary": summary}
 
 
 def run_single(args):
@@ -739,6 +766,11 @@ def measure_batched(args):
         "tune": tune.entries, "tune_seconds": tune_s,
         "clocks": clocks,
     }
+    short = {"per_cell_launches": "per_cell", "batched_default_tiles": "default",
+             "batched_tuned": "tuned", "batched_tuned_graph": "tuned_graph"}
+    line["summary"] = {"gbps": value, "ms": ms, "roofline_frac": t_bound * 1e3 / ms,
+                       "arms_gbps": {short[k]: bits / (v / 1e3) / 1e9 for k, v in arms.items()},
+                       "cells": len(cells)}
     return line
 
 
@@ -850,6 +882,8 @@ def measure_unfolded(args):
         "loss": float(g_loss.detach()),
         "clocks": sampler.summary(),
     }
+    line["summary"] = {"samples_per_s": samples / (ms / 1e3), "ms": ms, "forward_ms": ms_fwd,
+                       "roofline_frac": t_bound * 1e3 / ms}
     return line
 
 

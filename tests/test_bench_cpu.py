@@ -74,7 +74,7 @@ def test_cpu_baseline_line_reports_all_oracle_forms():
     import argparse
     line = bench.cpu_baseline_line(argparse.Namespace(cpu_seconds=0.4, mode="box"))
     assert line["kind"] == "oracle" and line["unit"] == "Gb/s" and line["value"] > 0
-    assert line["single_core"]["value"] > 0 and line["numpy_oracle"]["value"] > 0
+    assert line["single_core_gbps"] > 0 and line["numpy_oracle_gbps"] > 0
     assert line["cores"] >= 1
 
 
@@ -99,3 +99,8 @@ def test_commands_in_profiles_parse():
             bench.parser().parse_args(argv)
             found += 1
     assert found >= 4
+
+
+def test_summaries_are_rounded_to_four_digits():
+    out = bench._r({"a": 123.456789, "b": [0.000123456, 7], "c": {"d": 1e-9 / 3}, "e": "x"})
+    assert out == {"a": 123.5, "b": [0.0001235, 7], "c": {"d": 3.333e-10}, "e": "x"}
