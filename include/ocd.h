@@ -153,7 +153,12 @@ int ocd_detect_host(const void* H, const void* Y, int Nsc, int B, int U, int T,
  * launch found a cell's tensor map misaligned; in both cases the affected
  * subcarriers were left unwritten).  Returns the bits (>= 0) or
  * OCD_ERR_CUDA, and clears them when `clear` is non-zero.  Synchronizes with
- * the current device.
+ * the current device.  After a non-zero bit 0 the outputs of every launch
+ * enqueued since the last check are undefined, including those of the launch
+ * that follows the faulting one: a warp that gives up waits only a bounded
+ * time for its own copies still in flight, and a copy that lands later may
+ * overwrite shared memory the next launch's blocks are using.  Re-run those
+ * launches.
  */
 int ocd_fault_status(int clear);
 
@@ -245,7 +250,8 @@ int ocd_detect_batched(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tu
  * The counters are zeroed on `stream` at the start of every call.  All calls
  * on one device share them, so calls that overlap on the GPU race and give
  * wrong results: issue them on one stream, or order them with events.  The
- * first call on a device looks up the array's device address and sets up the
+ * first call on a device looks up the array's device address, creates the
+ * library's internal streams and events for that device and sets up the
  * device's kernel attributes; make that first call before any stream capture.
  */
 #define OCD_STATIC_MAX_CELLS 256

@@ -354,7 +354,10 @@ StaticScratch g_static[kMaxDevices];
 std::mutex g_static_mu;
 
 // Device address of g_static_tickets on `dev` (the current device), looked
-// up once per device.
+// up once per device.  The same first call also creates the device's
+// internal streams and events (what an enqueue of several kernel families
+// uses), so that no later call creates them, whether or not that later call
+// runs under a stream capture.
 int static_scratch(int dev, unsigned int*& out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(OCD_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
   std::lock_guard<std::mutex> lk(g_static_mu);
@@ -362,6 +365,12 @@ int static_scratch(int dev, unsigned int*& out) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_tickets);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    {
+      std::lock_guard<std::mutex> lk_hs(g_hs_mu);  // lock order: g_static_mu, then g_hs_mu
+      HostStreams* hs = nullptr;
+      const int st = host_streams(dev, hs);
+      if (st != OCD_OK) return st;
+    }
     g_static[dev].ptr = static_cast<unsigned int*>(p);
     g_static[dev].ready = true;
   }

@@ -60,6 +60,10 @@ def test_static_scratch_matches_the_workspace_entry_point_twice_in_a_row():
 
 
 def test_static_scratch_allocates_nothing():
+    """Neither PyTorch's allocator nor the device's free memory moves across
+    three calls.  The device-wide check assumes this process has the GPU to
+    itself for the duration of the test (one job per GPU), so that no other
+    process allocates or frees in between."""
     cells = make_cells(802)
     ocd.ocd_detect_batched_static(cells)  # first call on the device: address lookup
     torch.cuda.synchronize()
