@@ -116,54 +116,74 @@ __device__ __forceinline__ void project(float& wr, float& wi, const DetectParams
 }
 
 // Max-log LLRs (Eq. 9) of the bits carried by one real dimension with NB
-// bits (M = 2^NB levels).  For a separable Gray alphabet the minima over
-// O_b^0 and O_b^1 differ only in this dimension, so the other dimension's
-// contribution cancels exactly.  Level i sits at (2i + 1 - M) * step and
-// carries the Gray word i ^ (i >> 1); the loops unroll completely, so every
-// label test is resolved at compile time.
+// bits (M = 2^NB levels), in closed form.  For a separable Gray alphabet the
+// minima over O_b^0 and O_b^1 differ only in this dimension, so the other
+// dimension's contribution cancels exactly.  u = x / step is the coordinate
+// in level units: level i sits at u = 2i + 1 - M and carries the Gray word
+// i ^ (i >> 1), first bit most significant.
+//
+// First bit (1 on the positive levels): between consecutive even integers
+// the nearest level of either label is fixed, and
+//     d0 - d1 = sign(u) * max_{j = 1 .. M/2} 4 j (|u| - (j - 1))
+// in units of step^2 (the j-th line is the difference for nearest levels
+// -1 and 2j - 1; consecutive lines meet at the thresholds |u| = 2 (j - 1)),
+// which is the exhaustive difference of minima, not an approximation.
+// Folding u' = M/2 - |u| maps the positive half of the M-level Gray PAM onto
+// an M/2-level one centred at zero whose first bit (1 where u' > 0, the
+// inner levels) is the second bit of the original; a level across zero is
+// never nearer than its mirror image, so the same form gives every bit.
+// out[j] = rs2 * (d0 - d1) with rs2 = rho~ step^2.
 template <int NB>
-__device__ __forceinline__ void dimension_llr_nb(float x, float rho, float step, float* out) {
-  constexpr int M = 1 << NB;
-  float d0[NB], d1[NB];
+__device__ __forceinline__ void dimension_llr_nb(float u, float rs2, float* out) {
+  float v = u;
 #pragma unroll
-  for (int j = 0; j < NB; ++j) { d0[j] = FLT_MAX; d1[j] = FLT_MAX; }
+  for (int j = 0; j < NB; ++j) {
+    const int half = 1 << (NB - 1 - j);  // half the levels of this stage
+    const float a = fabsf(v);
+    if (half == 1) {
+      out[j] = rs2 * (4.0f * v);
+    } else {
+      float m = 4.0f * a;
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const float e = x - (float)(2 * i + 1 - M) * step;
-    const float d = e * e;
-    const int g = i ^ (i >> 1);
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      if ((g >> (NB - 1 - j)) & 1) d1[j] = fminf(d1[j], d);
-      else d0[j] = fminf(d0[j], d);
+      for (int l = 2; l <= half; ++l) m = fmaxf(m, fmaf(4.0f * l, a, -4.0f * l * (l - 1)));
+      out[j] = rs2 * copysignf(m, v);
     }
+    v = (float)half - a;
   }
-#pragma unroll
-  for (int j = 0; j < NB; ++j) out[j] = rho * (d0[j] - d1[j]);
 }
 
-__device__ __forceinline__ void dimension_llr(float x, float rho, const DetectParams& P,
+__device__ __forceinline__ void dimension_llr(float u, float rs2, const DetectParams& P,
                                               float* out) {
   switch (P.nb) {
-    case 1: dimension_llr_nb<1>(x, rho, P.lvl_step, out); break;
-    case 2: dimension_llr_nb<2>(x, rho, P.lvl_step, out); break;
-    case 3: dimension_llr_nb<3>(x, rho, P.lvl_step, out); break;
-    default: dimension_llr_nb<4>(x, rho, P.lvl_step, out); break;
+    case 1: dimension_llr_nb<1>(u, rs2, out); break;
+    case 2: dimension_llr_nb<2>(u, rs2, out); break;
+    case 3: dimension_llr_nb<3>(u, rs2, out); break;
+    default: dimension_llr_nb<4>(u, rs2, out); break;
   }
 }
 
-// Soft output of one user (Section III-C): mu~ = p, rho~ = ||h||^2 Es / N0,
-// LLRs of z / (mu~ sqrt(Es)) against the unit-energy alphabet.
+// Soft-output constants of one user (Section III-C): mu~ = p, rho~ =
+// ||h||^2 Es / N0.  u_scale: level units per unit of z, 1 / (mu~ sqrt(Es)
+// step) (0 when mu~ = 0); rs2: rho~ step^2.
+__device__ __forceinline__ float llr_u_scale(float p, const DetectParams& P) {
+  return p > 0.0f ? 1.0f / (p * P.sqrt_es * P.lvl_step) : 0.0f;
+}
+__device__ __forceinline__ float llr_rs2(float nrm, const DetectParams& P) {
+  return nrm * P.rho_scale * (P.lvl_step * P.lvl_step);
+}
+
+// Soft output of one user: LLRs of z / (mu~ sqrt(Es)) against the
+// unit-energy alphabet; a user with mu~ = 0 gets L = 0.
 __device__ __forceinline__ void user_llr(float2 z, float nrm, float p, const DetectParams& P,
                                          float* out) {
   if (!(p > 0.0f)) {
     for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
     return;
   }
-  const float inv = 1.0f / (p * P.sqrt_es);
-  const float rho = nrm * P.rho_scale;
-  dimension_llr(z.x * inv, rho, P, out);
-  if (!P.bpsk) dimension_llr(z.y * inv, rho, P, out + P.nb);
+  const float us = llr_u_scale(p, P);
+  const float rs2 = llr_rs2(nrm, P);
+  dimension_llr(z.x * us, rs2, P, out);
+  if (!P.bpsk) dimension_llr(z.y * us, rs2, P, out + P.nb);
 }
 
 }  // namespace ocd

@@ -296,8 +296,8 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
         const float p = dinv * nrm;
         spre[4 * lane] = dinv;
         spre[4 * lane + 1] = p;
-        spre[4 * lane + 2] = nrm;
-        spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
+        spre[4 * lane + 2] = llr_rs2(nrm, P);  // rho~ step^2
+        spre[4 * lane + 3] = llr_u_scale(p, P);  // level units per unit of z
         sg[h16_gim<NU>(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
@@ -372,6 +372,9 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     auto outputs = [&](auto nbc) {
       constexpr int NB = decltype(nbc)::value;
       const bool full_tile = U == NU;
+      // both dimensions' LLRs of an item stored as float2 pairs (Q = 2 NB is
+      // even, so every item starts 8-byte aligned when the array does)
+      const bool pairs = !P.bpsk && (reinterpret_cast<uintptr_t>(P.llr) & 7u) == 0;
       for (int f = lane; f < np * U; f += 32) {
         const int ts = full_tile ? f / NU : f / U;
         const int u = f - ts * U;
@@ -384,9 +387,18 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
           if (!(inv > 0.0f)) {
             for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
           } else {
-            const float rho = spre[4 * u + 2] * P.rho_scale;
-            dimension_llr_nb<NB>(z.x * inv, rho, P.lvl_step, out);
-            if (!P.bpsk) dimension_llr_nb<NB>(z.y * inv, rho, P.lvl_step, out + NB);
+            const float rs2 = spre[4 * u + 2];
+            if (pairs) {
+              float L[2 * NB];
+              dimension_llr_nb<NB>(z.x * inv, rs2, L);
+              dimension_llr_nb<NB>(z.y * inv, rs2, L + NB);
+#pragma unroll
+              for (int j = 0; j < 2 * NB; j += 2)
+                *reinterpret_cast<float2*>(out + j) = make_float2(L[j], L[j + 1]);
+            } else {
+              dimension_llr_nb<NB>(z.x * inv, rs2, out);
+              if (!P.bpsk) dimension_llr_nb<NB>(z.y * inv, rs2, out + NB);
+            }
           }
         }
       }

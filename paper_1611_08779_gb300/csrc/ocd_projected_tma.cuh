@@ -78,7 +78,7 @@ struct TmaShape {
   // per-warp byte offsets (the warp area is 1024-byte aligned for the swizzle)
   static constexpr int kOffQ = kStages * kBufBytes;         // q0, later z [pass symbol][u]
   static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;  // full G [i][j]
-  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
+  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, rho~ step^2, LLR level scale)
   static constexpr int kOffBar = kOffPre + 16 * kUsers;     // one mbarrier per buffer
   static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
   static_assert(kBB % kBoxAnt == 0, "blocks are whole Y boxes");
@@ -428,8 +428,8 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         const float p = dinv * nrm;
         spre[4 * lane] = dinv;
         spre[4 * lane + 1] = p;
-        spre[4 * lane + 2] = nrm;
-        spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
+        spre[4 * lane + 2] = llr_rs2(nrm, P);  // rho~ step^2
+        spre[4 * lane + 3] = llr_u_scale(p, P);  // level units per unit of z
         sg[tma_gim<NU>(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
@@ -511,6 +511,9 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
     auto outputs = [&](auto nbc) {
       constexpr int NB = decltype(nbc)::value;
       const bool full_tile = U == NU;
+      // both dimensions' LLRs of an item stored as float2 pairs (Q = 2 NB is
+      // even, so every item starts 8-byte aligned when the array does)
+      const bool pairs = !P.bpsk && (reinterpret_cast<uintptr_t>(P.llr) & 7u) == 0;
       for (int f = lane; f < np * U; f += 32) {
         const int ts = full_tile ? f / NU : f / U;
         const int u = f - ts * U;
@@ -523,9 +526,18 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
           if (!(inv > 0.0f)) {
             for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
           } else {
-            const float rho = spre[4 * u + 2] * P.rho_scale;
-            dimension_llr_nb<NB>(z.x * inv, rho, P.lvl_step, out);
-            if (!P.bpsk) dimension_llr_nb<NB>(z.y * inv, rho, P.lvl_step, out + NB);
+            const float rs2 = spre[4 * u + 2];
+            if (pairs) {
+              float L[2 * NB];
+              dimension_llr_nb<NB>(z.x * inv, rs2, L);
+              dimension_llr_nb<NB>(z.y * inv, rs2, L + NB);
+#pragma unroll
+              for (int j = 0; j < 2 * NB; j += 2)
+                *reinterpret_cast<float2*>(out + j) = make_float2(L[j], L[j + 1]);
+            } else {
+              dimension_llr_nb<NB>(z.x * inv, rs2, out);
+              if (!P.bpsk) dimension_llr_nb<NB>(z.y * inv, rs2, out + NB);
+            }
           }
         }
       }
@@ -549,9 +561,9 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
         if (!(inv > 0.0f)) {
           for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
         } else {
-          const float rho = spre[4 * u + 2] * P.rho_scale;
-          dimension_llr(z.x * inv, rho, P, out);
-          if (!P.bpsk) dimension_llr(z.y * inv, rho, P, out + P.nb);
+          const float rs2 = spre[4 * u + 2];
+          dimension_llr(z.x * inv, rs2, P, out);
+          if (!P.bpsk) dimension_llr(z.y * inv, rs2, P, out + P.nb);
         }
       }
     }

@@ -71,7 +71,7 @@ struct WideShape {
   static constexpr int kQBytes = 8 * kPass * kUsers;
   static_assert(kQBytes <= kBufBytes, "q0 fits in a staging buffer");
   static constexpr int kOffG = kStages * kBufBytes;         // G [i][j]
-  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, ||h||^2, 1/(mu sqrtEs))
+  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, rho~ step^2, LLR level scale)
   static constexpr int kOffBar = kOffPre + 16 * kUsers;
   static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
   static constexpr int kThreads = 32;                       // one warp per CTA
@@ -351,8 +351,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
         const float p = dinv * nrm;
         spre[4 * lane] = dinv;
         spre[4 * lane + 1] = p;
-        spre[4 * lane + 2] = nrm;
-        spre[4 * lane + 3] = p > 0.0f ? 1.0f / (p * P.sqrt_es) : 0.0f;
+        spre[4 * lane + 2] = llr_rs2(nrm, P);  // rho~ step^2
+        spre[4 * lane + 3] = llr_u_scale(p, P);  // level units per unit of z
         sg[wide_gim(lane, lane)] = 0.0f;  // G_uu is real
       }
       __syncwarp();
@@ -543,9 +543,9 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
         if (!(inv > 0.0f)) {
           for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
         } else {
-          const float rho = spre[4 * u + 2] * P.rho_scale;
-          dimension_llr(z.x * inv, rho, P, out);
-          if (!P.bpsk) dimension_llr(z.y * inv, rho, P, out + P.nb);
+          const float rs2 = spre[4 * u + 2];
+          dimension_llr(z.x * inv, rs2, P, out);
+          if (!P.bpsk) dimension_llr(z.y * inv, rs2, P, out + P.nb);
         }
       }
     }

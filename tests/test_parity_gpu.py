@@ -248,3 +248,26 @@ def test_projected_wide_shapes(B, U, T):
     """The 256x32 cells of the batched workload, B = 512, tiny B, T = 1."""
     check(4, B, U, T, 3, orc.BOX, 16, 15.0, B + U + T, label=f"{B}x{U} T{T}",
           algos=["projected"])
+
+
+@pytest.mark.parametrize("order", [4, 16, 64, 256])
+@pytest.mark.parametrize("U", [8, 16])
+def test_llr_array_only_4_byte_aligned(U, order):
+    """An LLR array that starts 4 bytes past an 8-byte boundary takes the
+    kernels' scalar store path (the paired float2 stores need 8-byte
+    alignment); both paths must give the oracle's values."""
+    d = synth.make_uplink(20, 64, U, 14, order, 15.0, 66 + U + order)
+    H = torch.from_numpy(d["H"]).cuda()
+    Y = torch.from_numpy(d["Y"]).cuda()
+    Q = orc.bits_per_symbol(order)
+    n = 20 * 14 * U * Q
+    for mode in (orc.MMSE, orc.BOX):
+        buf = torch.full((n + 1,), float("nan"), dtype=torch.float32, device="cuda")
+        llr = buf[1:].view(20, 14, U, Q)
+        assert llr.data_ptr() % 8 == 4
+        x, L = ocd.ocd_detect(H, Y, d["N0"], 1.0, 3, MODE[mode], order, llr=llr, algo="projected")
+        torch.cuda.synchronize()
+        assert L.data_ptr() == llr.data_ptr()
+        assert_parity(x.cpu().numpy(), L.cpu().numpy(), d["H"], d["Y"], d["N0"], 1.0, 3, mode,
+                      order, f"unaligned LLR U={U} order={order}")
+        assert bool(torch.isnan(buf[0]))  # the slot before the array is untouched
