@@ -42,7 +42,8 @@ FALLBACK_HBM_GBS = 6800.0
 SMS_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
-KERNEL_SOURCES = ["ocd_common.cuh", "ocd_mma.cuh", "ocd_projected_tma.cuh", "ocd_projected_tma.cu"]
+# device sources of the headline kernel (its host launch code is not part of it)
+KERNEL_SOURCES = ["ocd_common.cuh", "ocd_mma.cuh", "ocd_tma_util.cuh", "ocd_projected_tma.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ocd_projected_tma_128x8_t14_k3.md")
 MIN_CLOCK_WINDOW_S = 0.5
 REF_BUDGET_S = 60.0

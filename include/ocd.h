@@ -64,9 +64,26 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *                       16-byte aligned H and Y; else RESIDUAL.
  * For T == 1 and U <= 8 (float32 storage, even B, 16-byte aligned H and Y)
  * the projected form runs with one lane per subcarrier (G and q0 accumulated
- * in registers, no reduction across lanes).
+ * in registers, no reduction across lanes).  For 16 < U <= 32 and 9 <= T <= 16
+ * (float32 storage, even B, 16-byte aligned H and Y) its two products run on
+ * the fifth-generation tensor cores with accumulators in tensor memory (one
+ * CTA per SM, holding that SM's whole tensor memory while it runs); for the
+ * other shapes the warp-level tensor-core kernels are the faster ones.
+ *   OCD_ALGO_PROJECTED_WARP  the projected form with warp-level tensor-core
+ *                       products only.
+ *   OCD_ALGO_PROJECTED_TC    the projected form with the tensor-memory kernel
+ *                       for any shape it supports (16 < U <= 32, T <= 16, the
+ *                       storage and alignment above); OCD_ERR_UNSUPPORTED
+ *                       otherwise.  Not available in the batched form.
+ * All projected kernels give the same results up to FP32 rounding.
  */
-typedef enum { OCD_ALGO_AUTO = 0, OCD_ALGO_RESIDUAL = 1, OCD_ALGO_PROJECTED = 2 } ocd_algo_t;
+typedef enum {
+  OCD_ALGO_AUTO = 0,
+  OCD_ALGO_RESIDUAL = 1,
+  OCD_ALGO_PROJECTED = 2,
+  OCD_ALGO_PROJECTED_WARP = 3,
+  OCD_ALGO_PROJECTED_TC = 4
+} ocd_algo_t;
 
 /*
  * Storage of H and Y (outputs are always float32): interleaved complex as

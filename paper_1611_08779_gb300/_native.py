@@ -23,6 +23,8 @@ OCD_STORE_F16 = 2
 OCD_ALGO_AUTO = 0
 OCD_ALGO_RESIDUAL = 1
 OCD_ALGO_PROJECTED = 2
+OCD_ALGO_PROJECTED_WARP = 3
+OCD_ALGO_PROJECTED_TC = 4
 OCD_MAX_USERS = 32
 OCD_MAX_ANTENNAS = 512
 OCD_MAX_SWEEPS = 256

@@ -18,7 +18,9 @@ MODES = {"mmse": _native.OCD_MMSE, "box": _native.OCD_BOX,
 
 
 ALGOS = {"auto": _native.OCD_ALGO_AUTO, "residual": _native.OCD_ALGO_RESIDUAL,
-         "projected": _native.OCD_ALGO_PROJECTED}
+         "projected": _native.OCD_ALGO_PROJECTED,
+         "projected_warp": _native.OCD_ALGO_PROJECTED_WARP,
+         "projected_tc": _native.OCD_ALGO_PROJECTED_TC}
 
 
 def bits_per_symbol(qam_order: int) -> int:
@@ -79,7 +81,8 @@ def ocd_detect(H: torch.Tensor, Y: torch.Tensor, N0: float, Es: float = 1.0, K: 
     H: [Nsc, B, U] and Y: [Nsc, T, B] complex on one CUDA device, both
     complex64, or both 16-bit pairs (complex32, or bfloat16 / float16 with a
     trailing dimension of 2 holding (re, im)).
-    `algo` picks the arrangement ("auto", "residual" or "projected"; see
+    `algo` picks the arrangement ("auto", "residual", "projected",
+    "projected_warp" or "projected_tc"; see
     include/ocd.h).  Returns (xhat complex64 [Nsc, T, U] or None,
     llr float32 [Nsc, T, U, Q] or None).
     The work is enqueued on `stream` (default: the current stream); nothing

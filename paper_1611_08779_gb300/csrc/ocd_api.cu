@@ -125,7 +125,8 @@ int device_info(int dev, DeviceInfo& out) {
     }
     for (const void* fn : {ocd::projected_wide_kernel_ptr(),
                            reinterpret_cast<const void*>(ocd::batched_wide_kernel(false)),
-                           reinterpret_cast<const void*>(ocd::batched_wide_kernel(true))}) {
+                           reinterpret_cast<const void*>(ocd::batched_wide_kernel(true)),
+                           ocd::projected_tc_kernel_ptr(1), ocd::projected_tc_kernel_ptr(16)}) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
@@ -179,7 +180,8 @@ int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl
 int validate(const void* H, const void* Y, int storage, int Nsc, int B, int U, int T, float N0,
              float Es, int K, int mode, int qam_order, const void* xhat, const void* llr, int algo,
              Alphabet& al) {
-  if (algo != OCD_ALGO_AUTO && algo != OCD_ALGO_RESIDUAL && algo != OCD_ALGO_PROJECTED)
+  if (algo != OCD_ALGO_AUTO && algo != OCD_ALGO_RESIDUAL && algo != OCD_ALGO_PROJECTED &&
+      algo != OCD_ALGO_PROJECTED_WARP && algo != OCD_ALGO_PROJECTED_TC)
     return fail(OCD_ERR_ARG, "unknown algo %d", algo);
   if (storage != OCD_STORE_C64 && storage != OCD_STORE_BF16 && storage != OCD_STORE_F16)
     return fail(OCD_ERR_ARG, "unknown storage %d", storage);
@@ -219,6 +221,17 @@ bool can_wide(const ocd::DetectParams& P) {
   return P.storage == ocd::kStoreC64 && P.U > ocd::kTmaMaxUsers && P.U <= ocd::kWideMaxUsers &&
          P.B % 2 == 0 && aligned16(P);
 }
+// tcgen05 products for 16 < U <= 32 with at most 16 symbols per subcarrier
+// (float32 storage, even B, 16-byte aligned bases).
+bool can_tc(const ocd::DetectParams& P) {
+  return can_wide(P) && P.T <= ocd::kTcMaxSymbols;
+}
+// Where the projected form takes the tcgen05 kernel by default: measured
+// faster than the warp-level kernel for 9..16 symbols (256x32, T = 14: 0.251
+// against 0.262 ms); at T <= 8 the warp-level kernel, which then folds q0 into
+// its G phase, is faster (T = 7: 0.190 against 0.225 ms; T = 1: 0.667 against
+// 0.760 ms).
+bool prefer_tc(const ocd::DetectParams& P) { return can_tc(P) && P.T > 8; }
 // One lane per subcarrier: one symbol, float32 storage, U <= 8, even B,
 // 16-byte aligned bases.
 bool can_lane(const ocd::DetectParams& P) {
@@ -261,11 +274,30 @@ int lane_grid(const ocd::DetectParams& P, const DeviceInfo& di, unsigned& grid) 
   return OCD_OK;
 }
 
-int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, cudaStream_t stream) {
+// use_tc: run the tcgen05 kernel (the caller has checked can_tc); false
+// keeps the warp-level MMA kernels.
+int launch_projected(ocd::DetectParams& P, const DeviceInfo& di, int U, bool use_tc,
+                     cudaStream_t stream) {
   const int nt = 128;
   const long long need = (P.Nsc + nt / 32 - 1) / (nt / 32);  // one warp per subcarrier
   int per_sm = 0;
   cudaError_t e;
+  if (use_tc) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ocd::projected_tc_kernel_ptr(P.T),
+                                                      ocd::projected_tc_threads(),
+                                                      ocd::projected_tc_smem_per_cta(P.T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm >= 1) {
+      // one CTA per SM (it holds the SM's whole tensor memory), persistent
+      long long grid = di.sms;
+      if (grid > P.Nsc) grid = P.Nsc;
+      e = ocd::launch_projected_tc(P, (unsigned)grid, stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) return OCD_OK;
+      return cuda_fail(e, "projected tcgen05 kernel launch");
+    }
+    return fail(OCD_ERR_UNSUPPORTED, "tcgen05 kernel cannot be resident");
+  }
   if (can_lane(P)) {
     unsigned grid = 0;
     const int st = lane_grid(P, di, grid);
@@ -371,11 +403,17 @@ int launch_detect(const void* H, const void* Y, int storage, int Nsc, int B, int
   if (st != OCD_OK) return st;
 
   algo = resolve_algo(algo, P);
-  if (algo == OCD_ALGO_PROJECTED) {
+  if (algo == OCD_ALGO_PROJECTED_TC) {
+    if (!can_tc(P))
+      return fail(OCD_ERR_UNSUPPORTED, "the tcgen05 kernel needs 16 < U <= 32, T <= %d, float32 "
+                  "storage, even B and 16-byte aligned H and Y", ocd::kTcMaxSymbols);
+    return launch_projected(P, di, U, true, stream);
+  }
+  if (algo == OCD_ALGO_PROJECTED || algo == OCD_ALGO_PROJECTED_WARP) {
     if (!can_projected(P))
       return fail(OCD_ERR_UNSUPPORTED, "projected form does not support U=%d with this storage "
                   "and alignment", U);
-    return launch_projected(P, di, U, stream);
+    return launch_projected(P, di, U, algo == OCD_ALGO_PROJECTED && prefer_tc(P), stream);
   }
 
   // Keep several CTAs per SM when the staged channels allow it; otherwise

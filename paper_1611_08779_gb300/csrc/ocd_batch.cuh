@@ -45,6 +45,8 @@ BatchFn batched_tma_kernel(int U);
 // Tensor map of Y for the bulk-copy kernels; cudaErrorNotSupported when the
 // driver offers no tensor-map encoder.
 cudaError_t encode_ymap(const DetectParams& P, CUtensorMap* map);
+// The same with a box of `rows` received rows (16 antennas wide).
+cudaError_t encode_ymap_rows(const DetectParams& P, CUtensorMap* map, int rows);
 // Staged steps (antenna blocks x symbol passes) per subcarrier of the
 // bulk-copy kernels.
 int tma_steps_per_sc(int B, int T);
@@ -61,5 +63,13 @@ cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStre
 bool wide_fuses(int T);
 BatchFn batched_wide_kernel(bool fused);
 cudaError_t projected_wide_fault(unsigned int* bits, bool clear);
+// The same products on the fifth-generation tensor cores (tcgen05, TMEM
+// accumulators) for 16 < U <= 32, T <= 16 (float32 storage, even B, 16-byte
+// aligned H and Y): one 320-thread CTA per SM holding the SM's whole TMEM.
+constexpr int kTcMaxSymbols = 16;
+const void* projected_tc_kernel_ptr(int T);
+size_t projected_tc_smem_per_cta(int T);
+int projected_tc_threads();
+cudaError_t launch_projected_tc(const DetectParams& P, unsigned grid, cudaStream_t stream);
 
 }  // namespace ocd

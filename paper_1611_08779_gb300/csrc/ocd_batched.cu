@@ -77,6 +77,9 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   const bool wide = can_wide(cp.P);
   const bool tma_ok = can_tma32(cp.P) || wide;
   int algo = c.algo;
+  if (algo == OCD_ALGO_PROJECTED_TC)
+    return fail(OCD_ERR_UNSUPPORTED, "cell %d: the batched form has no tcgen05 kernel", index);
+  if (algo == OCD_ALGO_PROJECTED_WARP) algo = OCD_ALGO_PROJECTED;  // the batched kernels are warp-level
   if (algo == OCD_ALGO_AUTO && te && (te->algo == OCD_ALGO_RESIDUAL || te->algo == OCD_ALGO_PROJECTED))
     algo = te->algo;
   // default without a tune entry: the bulk-copy projected form wherever it

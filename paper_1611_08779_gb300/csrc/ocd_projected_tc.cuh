@@ -1,0 +1,422 @@
+// Projected-residual OCD for 17 to 32 users with the two per-subcarrier
+// products on the fifth-generation tensor cores (tcgen05, accumulators in
+// tensor memory).  Same algebra as the warp-level 32-user kernel
+// (ocd_projected_wide.cuh): q0 = H^H Y^T and G = H^H H per subcarrier, then
+// the K sweeps of Algorithm 1 on q = H^H r.
+//
+// Realified products over K = 2B (antenna a, part c): with the operand rows
+//     Re-row u:  (Re h_{a,u}, Im h_{a,u})_a      Im-row u:  (-Im h_{a,u}, Re h_{a,u})_a
+//     Y-row t:   (Re y_{t,a}, Im y_{t,a})_a       (the received row as stored)
+// the dot product of Re-row u with Y-row t is Re(h_u^H y_t) and of Im-row u
+// with it Im(h_u^H y_t); with Re-row j in place of the Y-row they give
+// Re G_uj and Im G_uj.  So one shared-memory buffer per staged block holds
+// the rows [Y (YR) | Re (32) | Im (32)], and ONE MMA per K slice with
+//     A = rows YR .. YR + 63 (M = 64),  B = rows 0 .. YR + 31 (N = YR + 32)
+// accumulates q0 (columns 0 .. YR - 1) and G (columns YR .. YR + 31) at once.
+// FP32-level accuracy: A B^T = Ah Bh^T + Ah Bl^T + Al Bh^T with hi = the value
+// as stored (the tensor core reads the leading 19 bits of an FP32 operand:
+// it truncates, measured) and lo = value - trunc(value); the dropped Al Bl^T
+// and the truncation of lo leave about 2^-20 relative error per product.
+//
+// One CTA (10 warps) per SM, persistent over subcarriers blockIdx.x +
+// i gridDim.x, blocks of 16 antennas (one 128-byte K atom per operand row):
+//   warp 0      producer: per block a bulk copy of the 16 channel rows and a
+//               2-D tensor copy of the YR received rows (128-byte swizzle, the
+//               operand layout itself) into a deep ring of raw stages, so
+//               that about 70 KB per SM are in flight;
+//   warps 2-5   transform: raw stage -> operand stage (a shallower ring):
+//               channel rows -> Re/Im rows (hi and lo), received rows copied
+//               with their lo rows;
+//   warp 1      one thread issues 3 MMAs per K slice of 8 into the
+//               subcarrier's TMEM slot and commits each block (the stage is
+//               free again) and each subcarrier (accumulators ready);
+//   warps 6-9   epilogue, one per TMEM lane quarter: groups of 4 subcarriers
+//               are drained from TMEM together (an M = 64 accumulator keeps
+//               row 16q + i in lane 32q + i), then each warp runs the
+//               preprocessing, the K sweeps and the outputs of one of them.
+// Eight TMEM slots of 64 columns (two groups of four) let the MMAs of one
+// group run under the epilogue of the previous one.  Every wait is bounded
+// in wall time; a wait that expires sets the fault word and a shared abort
+// flag that ends every role's loop, and the async copies and MMAs in flight
+// are waited for (bounded) before the TMEM is released.
+#pragma once
+
+#include "ocd_projected_wide.cuh"
+#include "ocd_tcgen05.cuh"
+
+namespace ocd {
+
+#ifndef OCD_TC_RAW_STAGES
+#define OCD_TC_RAW_STAGES 6   // pair blocks whose copies may be in flight (72 KB per SM)
+#endif
+#ifndef OCD_TC_OP_STAGES
+#define OCD_TC_OP_STAGES 2    // operand buffers (transform ahead of the MMAs)
+#endif
+
+// Two subcarriers a, b share every MMA ("pair"): the operand rows are
+//   [Y_a (YR) | Y_b (YR) | Re_a (32) | Re_b (32) | Im_a (32) | Im_b (32)]
+// with A = the last 128 rows (M = 128: TMEM lane i = row i) and B = the first
+// 2 YR + 64 rows (N = 2 YR + 64); the accumulator blocks that mix a with b
+// are computed and dropped.
+template <int YR>
+struct TcShape {
+  static_assert(YR == 8 || YR == 16, "received rows per subcarrier: 8 or 16");
+  static constexpr int kBA = 16;                          // antennas per staged block
+  static constexpr int kN = 2 * YR + 64;                  // MMA N
+  static constexpr int kRowA = 2 * YR;                    // first A row
+  static constexpr int kRows = 2 * YR + 128;              // operand rows
+  static constexpr int kOpBytes = kRows * 128;            // one operand buffer (hi or lo)
+  static constexpr int kOpStageBytes = 2 * kOpBytes;      // hi and lo
+  static constexpr int kOpStages = OCD_TC_OP_STAGES;
+  // raw stage: Y_a, Y_b boxes (swizzled, each YR rows), then H_a, H_b
+  static constexpr int kRawY = YR * 128;                  // one subcarrier's received rows
+  static constexpr int kRawH = kBA * 32 * 8;              // one subcarrier's channel rows
+  static constexpr int kRawStageBytes = 2 * kRawY + 2 * kRawH;
+  static constexpr int kRawStages = OCD_TC_RAW_STAGES;
+  static constexpr int kSlots = 4;                        // TMEM accumulator slots (pairs)
+  static constexpr int kSlotCols = 128;
+  static constexpr int kTmemCols = kSlots * kSlotCols;    // 512: the whole TMEM of an SM
+  static constexpr int kEpiG = 32 * WideShape::kGRow * 4;  // G rows (re run | im run | pad)
+  static constexpr int kEpiQ = 16 * 32 * 8;               // q0, then z, [symbol][user]
+  static constexpr int kEpiPre = 32 * 16;                 // (d^-1, p, rho~ step^2, u scale)
+  static constexpr int kEpiBytes = kEpiG + kEpiQ + kEpiPre;
+  static constexpr int kOffRaw = kOpStages * kOpStageBytes;
+  static constexpr int kOffEpi = kOffRaw + kRawStages * kRawStageBytes;
+  static constexpr int kOffBar = kOffEpi + 4 * kEpiBytes;
+  static constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 * kSlots;
+  static constexpr int kOffTmem = kOffBar + 8 * kNumBars;
+  static constexpr int kOffAbort = kOffTmem + 4;
+  static constexpr int kBytes = kOffAbort + 4;
+  static constexpr int kTransformWarps = 8;
+  static constexpr int kThreads = 32 * (2 + kTransformWarps + 4);  // 448
+  static_assert(kOpBytes % 1024 == 0 && kRawY % 1024 == 0 && kRawStageBytes % 1024 == 0,
+                "1024-byte swizzle phase");
+  static_assert(kN <= kSlotCols && kN % 16 == 0, "one pair's accumulators fit a slot");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Bounded wait that also gives up when another role has aborted; an expired
+// limit sets the abort flag and bit 0 of the fault word.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns,
+                                        volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 >= limit_ns) {
+      *abort_flag = 1;
+      atomicOr(&g_wide_fault, 1u);
+      return false;
+    }
+  }
+}
+// The same for all 32 lanes of a warp, with one warp-uniform result.
+__device__ __forceinline__ bool tc_wait_warp(uint32_t bar, uint32_t parity,
+                                             unsigned long long limit_ns, volatile int* abort_flag) {
+  const bool ok = tc_wait(bar, parity, limit_ns, abort_flag);
+  return __all_sync(kFullMask, ok);
+}
+
+// x - trunc_TF32(x) for the four values of a 16-byte chunk.
+__device__ __forceinline__ float4 tf32_lo4(float4 v) {
+  auto lo = [](float x) { return x - __uint_as_float(__float_as_uint(x) & 0xffffe000u); };
+  return make_float4(lo(v.x), lo(v.y), lo(v.z), lo(v.w));
+}
+
+template <int YR>
+__global__ void __launch_bounds__(TcShape<YR>::kThreads, 1)
+ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
+                        const __grid_constant__ CUtensorMap ymap) {
+  using S = TcShape<YR>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const uint32_t sbase = smem_addr(base);
+  const uint32_t bars = sbase + S::kOffBar;
+  constexpr int R = S::kRawStages;
+  constexpr int O = S::kOpStages;
+  constexpr int NTW = S::kTransformWarps;
+  constexpr int EW0 = 2 + NTW;  // first epilogue warp
+  auto bar_full = [&](int s) { return bars + 8u * s; };                 // raw stage landed
+  auto bar_free = [&](int s) { return bars + 8u * (R + s); };           // raw stage read
+  auto bar_ready = [&](int s) { return bars + 8u * (2 * R + s); };      // operands written
+  auto bar_empty = [&](int s) { return bars + 8u * (2 * R + O + s); };  // operands consumed
+  auto bar_accfull = [&](int j) { return bars + 8u * (2 * R + 2 * O + j); };
+  auto bar_accempty = [&](int j) { return bars + 8u * (2 * R + 2 * O + S::kSlots + j); };
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(base + S::kOffAbort);
+
+  const int B = P.B;
+  const int U = P.U;
+  const int T = P.T;
+  const int nblk = (B + S::kBA - 1) / S::kBA;
+  // this CTA's subcarriers: item i is subcarrier first + i * stride; pair p
+  // holds items 2p (half a) and 2p + 1 (half b, absent past the last item)
+  const long long first = blockIdx.x;
+  const long long stride = gridDim.x;
+  const long long nitems = first < P.Nsc ? (P.Nsc - 1 - first) / stride + 1 : 0;
+  const long long npairs = (nitems + 1) / 2;
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) {
+      mbar_init(bar_full(s), 1);
+      mbar_init(bar_free(s), NTW);
+    }
+    for (int s = 0; s < O; ++s) {
+      mbar_init(bar_ready(s), NTW);
+      mbar_init(bar_empty(s), 1);
+    }
+    for (int j = 0; j < S::kSlots; ++j) {
+      mbar_init(bar_accfull(j), 1);
+      mbar_init(bar_accempty(j), 4);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(sbase + S::kOffTmem, S::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(base + S::kOffTmem);
+
+  if (warp == 0) {
+    // ---------------- producer -------------------------------------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ymap)) : "memory");
+      long long g = 0;
+      bool ok = true;
+      for (long long p = 0; p < npairs && ok; ++p) {
+        const bool has_b = 2 * p + 1 < nitems;
+        const long long sca = first + 2 * p * stride;
+        for (int blk = 0; blk < nblk; ++blk, ++g) {
+          const int st = (int)(g % R);
+          const long long n = g / R;
+          if (n > 0 && !tc_wait(bar_free(st), (uint32_t)((n - 1) & 1), P.wait_ns, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int b0 = blk * S::kBA;
+          const int bb = min(S::kBA, B - b0);
+          const uint32_t hbytes = (uint32_t)(bb * U * 8);
+          const uint32_t stp = sbase + S::kOffRaw + st * S::kRawStageBytes;
+          fence_proxy_async();
+          mbar_expect_tx(bar_full(st), (has_b ? 2u : 1u) * (hbytes + (uint32_t)S::kRawY));
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has_b) break;
+            const long long sc = sca + h * stride;
+            tma_load_2d(stp + h * S::kRawY, &ymap, 2 * b0, (int)(sc * T), bar_full(st));
+            bulk_g2s(stp + 2 * S::kRawY + h * S::kRawH, P.H + (sc * (long long)B + b0) * U, hbytes,
+                     bar_full(st));
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies in flight land before the CTA can end
+        for (long long gg = g - R > 0 ? g - R : 0; gg < g; ++gg)
+          mbar_wait(bar_full((int)(gg % R)), (uint32_t)((gg / R) & 1), P.wait_ns);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc(128, S::kN);
+      long long g = 0;
+      bool ok = true;
+      for (long long p = 0; p < npairs && ok; ++p) {
+        const int slot = (int)(p % S::kSlots);
+        const long long m = p / S::kSlots;
+        if (m > 0 && !tc_wait(bar_accempty(slot), (uint32_t)((m - 1) & 1), P.wait_ns, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tbase + (uint32_t)(slot * S::kSlotCols);
+        for (int blk = 0; blk < nblk; ++blk, ++g) {
+          const int st = (int)(g % O);
+          if (!tc_wait(bar_ready(st), (uint32_t)((g / O) & 1), P.wait_ns, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          // descriptors of the stage; the K slices are 32 bytes (2 units of
+          // the start-address field) apart
+          const uint32_t hi = sbase + st * S::kOpStageBytes;
+          const uint64_t ah = sw128_desc(hi + S::kRowA * 128);
+          const uint64_t al = sw128_desc(hi + S::kOpBytes + S::kRowA * 128);
+          const uint64_t bh = sw128_desc(hi);
+          const uint64_t bl = sw128_desc(hi + S::kOpBytes);
+          tc_mma_tf32(d, ah, bh, idesc, blk > 0 ? 1u : 0u);
+          tc_mma_tf32(d, ah, bl, idesc, 1u);
+          tc_mma_tf32(d, al, bh, idesc, 1u);
+#pragma unroll
+          for (int ks = 1; ks < 4; ++ks) {
+            tc_mma_tf32(d, ah + 2 * ks, bh + 2 * ks, idesc, 1u);
+            tc_mma_tf32(d, ah + 2 * ks, bl + 2 * ks, idesc, 1u);
+            tc_mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
+          }
+          tc_commit(bar_empty(st));
+        }
+        if (!ok) break;
+        tc_commit(bar_accfull(slot));
+      }
+      // no MMA may still run when the TMEM is released: wait (bounded) for
+      // the commit that covers the last one issued
+      if (g > 0) mbar_wait(bar_empty((int)((g - 1) % O)), (uint32_t)(((g - 1) / O) & 1), P.wait_ns);
+    }
+    __syncwarp();
+  } else if (warp < EW0) {
+    // ---------------- transform -------------------------------------------
+    const int tt = tid - 64;  // 0 .. 32 NTW - 1
+    long long g = 0;
+    bool ok = true;
+    for (long long p = 0; p < npairs && ok; ++p) {
+      for (int blk = 0; blk < nblk; ++blk, ++g) {
+        const int rs = (int)(g % R);
+        const int os = (int)(g % O);
+        if (!tc_wait_warp(bar_full(rs), (uint32_t)((g / R) & 1), P.wait_ns, abort_flag) ||
+            (g >= O && !tc_wait_warp(bar_empty(os), (uint32_t)((g / O - 1) & 1), P.wait_ns,
+                                     abort_flag))) {
+          ok = false;
+          break;
+        }
+        const int bb = min(S::kBA, B - blk * S::kBA);
+        unsigned char* hi = base + os * S::kOpStageBytes;
+        unsigned char* lo = hi + S::kOpBytes;
+        const unsigned char* rawst = base + S::kOffRaw + rs * S::kRawStageBytes;
+        // channel: item = (half h, user u, antenna pair ap) -> one 16-byte
+        // chunk of K (antennas 2ap, 2ap + 1) in the Re-row and the Im-row of
+        // u (an absent half b transforms stale data into rows nobody reads)
+#pragma unroll
+        for (int j = 0; j < 512 / (32 * NTW); ++j) {
+          const int item = tt + 32 * NTW * j;
+          const int h = item >> 8;
+          const int u = item & 31;
+          const int ap = (item >> 5) & 7;
+          const int a0 = 2 * ap;
+          const float2* raw = reinterpret_cast<const float2*>(rawst + 2 * S::kRawY + h * S::kRawH);
+          const bool uok = u < U;
+          const float2 z2 = make_float2(0.0f, 0.0f);
+          const float2 h0 = (uok && a0 < bb) ? raw[a0 * U + u] : z2;
+          const float2 h1 = (uok && a0 + 1 < bb) ? raw[(a0 + 1) * U + u] : z2;
+          const float4 rh = make_float4(h0.x, h0.y, h1.x, h1.y);
+          const float4 ih = make_float4(-h0.y, h0.x, -h1.y, h1.x);
+          const int rr = S::kRowA + 32 * h + u;
+          const int ri = S::kRowA + 64 + 32 * h + u;
+          const int orr = rr * 128 + ((ap ^ (rr & 7)) << 4);
+          const int ori = ri * 128 + ((ap ^ (ri & 7)) << 4);
+          *reinterpret_cast<float4*>(hi + orr) = rh;
+          *reinterpret_cast<float4*>(lo + orr) = tf32_lo4(rh);
+          *reinterpret_cast<float4*>(hi + ori) = ih;
+          *reinterpret_cast<float4*>(lo + ori) = tf32_lo4(ih);
+        }
+        // received rows of both halves, as staged (the same swizzled layout)
+        // and their lo parts
+        for (int c = tt; c < 2 * YR * 8; c += 32 * NTW) {
+          const float4 v = *reinterpret_cast<const float4*>(rawst + 16 * c);
+          *reinterpret_cast<float4*>(hi + 16 * c) = v;
+          *reinterpret_cast<float4*>(lo + 16 * c) = tf32_lo4(v);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(bar_free(rs));
+          mbar_arrive(bar_ready(os));
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue --------------------------------------------
+    // TMEM lane quarter q = rows 32q .. 32q + 31: Re_a, Re_b, Im_a, Im_b;
+    // lane = user
+    const int q = warp & 3;
+    const int ew = warp - EW0;                   // member of a group this warp finishes
+    const int half = q & 1;
+    const int part = q >> 1;                     // 0: real parts, 1: imaginary parts
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int cq = half * YR;                    // this warp's q0 columns
+    const int cg = 2 * YR + 32 * half;           // this warp's G columns
+    // groups of two pairs (four subcarriers, one per epilogue warp)
+    for (long long p0 = 0; p0 < npairs; p0 += 2) {
+      named_bar_sync(1, 128);  // every member's buffers are free
+      for (int jp = 0; jp < 2; ++jp) {
+        const long long p = p0 + jp;
+        if (p >= npairs) break;
+        const int slot = (int)(p % S::kSlots);
+        if (!tc_wait_warp(bar_accfull(slot), (uint32_t)((p / S::kSlots) & 1), P.wait_ns,
+                          abort_flag))
+          continue;  // aborted: skip the work, keep the barriers in step
+        tc_fence_after();
+        uint32_t vq[16], vg0[16], vg1[16];
+        const uint32_t ta = tbase + lane_base + (uint32_t)(slot * S::kSlotCols);
+        tmem_ld16(ta + cq, vq);
+        tmem_ld16(ta + cg, vg0);
+        tmem_ld16(ta + cg + 16, vg1);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_accempty(slot));
+        if (2 * p + half >= nitems) continue;  // absent half b
+        unsigned char* eb = base + S::kOffEpi + (2 * jp + half) * S::kEpiBytes;
+        float* sg = reinterpret_cast<float*>(eb);
+        float* sq = reinterpret_cast<float*>(eb + S::kEpiG);
+#pragma unroll
+        for (int t = 0; t < YR; ++t)
+          if (t < T) sq[2 * (t * 32 + lane) + part] = __uint_as_float(vq[t]);
+        // row `lane`'s run of real or imaginary parts as 8 chunks of 4 (the
+        // row pad puts the lanes' rows on distinct bank positions)
+        float4* row = reinterpret_cast<float4*>(sg + (part ? wide_gim(lane, 0) : wide_gre(lane, 0)));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          row[c] = make_float4(__uint_as_float(vg0[4 * c]), __uint_as_float(vg0[4 * c + 1]),
+                               __uint_as_float(vg0[4 * c + 2]), __uint_as_float(vg0[4 * c + 3]));
+          row[4 + c] = make_float4(__uint_as_float(vg1[4 * c]), __uint_as_float(vg1[4 * c + 1]),
+                                   __uint_as_float(vg1[4 * c + 2]), __uint_as_float(vg1[4 * c + 3]));
+        }
+      }
+      named_bar_sync(1, 128);  // every member's G and q0 are in shared memory
+      const long long i = 2 * p0 + ew;  // member ew: pair p0 + ew / 2, half ew % 2
+      if (i < nitems && !*abort_flag) {
+        unsigned char* eb = base + S::kOffEpi + ew * S::kEpiBytes;
+        float* sg = reinterpret_cast<float*>(eb);
+        float* sq = reinterpret_cast<float*>(eb + S::kEpiG);
+        float* spre = reinterpret_cast<float*>(eb + S::kEpiG + S::kEpiQ);
+        {
+          // preprocessing of Algorithm 1 and the soft-output constants
+          const float nrm = sg[wide_gre(lane, lane)];
+          const float den = nrm + P.alpha;
+          const float dinv = (lane < U && den > 0.0f) ? 1.0f / den : 0.0f;
+          const float pu = dinv * nrm;
+          spre[4 * lane] = dinv;
+          spre[4 * lane + 1] = pu;
+          spre[4 * lane + 2] = llr_rs2(nrm, P);
+          spre[4 * lane + 3] = llr_u_scale(pu, P);
+          sg[wide_gim(lane, lane)] = 0.0f;  // G_uu is real
+        }
+        __syncwarp();
+        wide_sweeps_outputs(P, sq, sg, spre, first + i * stride, 0, T);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, S::kTmemCols);
+  }
+}
+
+}  // namespace ocd

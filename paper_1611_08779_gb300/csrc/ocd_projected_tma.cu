@@ -38,12 +38,16 @@ size_t projected_tma_smem_per_cta(int U) {
 int projected_tma_threads() { return 32 * OCD_TMA_WARPS; }
 
 cudaError_t encode_ymap(const DetectParams& P, CUtensorMap* map) {
+  return encode_ymap_rows(P, map, TmaShape<1>::kPass);
+}
+
+cudaError_t encode_ymap_rows(const DetectParams& P, CUtensorMap* map, int rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   // Y as a 2-D float tensor: rows = (subcarrier, symbol), 2B floats per row.
   const cuuint64_t dims[2] = {2ull * (cuuint64_t)P.B, (cuuint64_t)P.Nsc * (cuuint64_t)P.T};
   const cuuint64_t strides[1] = {2ull * (cuuint64_t)P.B * sizeof(float)};
-  const cuuint32_t box[2] = {2 * TmaShape<1>::kBoxAnt, TmaShape<1>::kPass};
+  const cuuint32_t box[2] = {2 * TmaShape<1>::kBoxAnt, (cuuint32_t)rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(P.Y), dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -1,5 +1,6 @@
-// Bulk-copy projected OCD kernels for up to 32 users: launch, the batched
-// kernel pointer and the fault word.
+// Bulk-copy projected OCD kernels for up to 32 users (warp-level MMA and
+// tcgen05 products): launch, the batched kernel pointer and the fault word.
+#include "ocd_projected_tc.cuh"
 #include "ocd_projected_wide.cuh"
 
 namespace ocd {
@@ -20,6 +21,27 @@ cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStre
   void* args[] = {&p, &map};
   return cudaLaunchKernel(projected_wide_kernel_ptr(), dim3(grid), dim3(WideShape::kThreads), args,
                           projected_wide_smem_per_cta(), stream);
+}
+
+const void* projected_tc_kernel_ptr(int T) {
+  return T <= 8 ? reinterpret_cast<const void*>(ocd_projected_tc_kernel<8>)
+                : reinterpret_cast<const void*>(ocd_projected_tc_kernel<16>);
+}
+
+size_t projected_tc_smem_per_cta(int T) {
+  return (T <= 8 ? TcShape<8>::kBytes : TcShape<16>::kBytes) + 1024;
+}
+
+int projected_tc_threads() { return TcShape<16>::kThreads; }
+
+cudaError_t launch_projected_tc(const DetectParams& P, unsigned grid, cudaStream_t stream) {
+  CUtensorMap map;
+  const cudaError_t e = encode_ymap_rows(P, &map, P.T <= 8 ? 8 : 16);
+  if (e != cudaSuccess) return e;
+  DetectParams p = P;
+  void* args[] = {&p, &map};
+  return cudaLaunchKernel(projected_tc_kernel_ptr(P.T), dim3(grid), dim3(projected_tc_threads()),
+                          args, projected_tc_smem_per_cta(P.T), stream);
 }
 
 bool wide_fuses(int T) { return OCD_WIDE_FUSE && T <= 8; }

@@ -71,19 +71,22 @@ struct WideShape {
   static constexpr int kQBytes = 8 * kPass * kUsers;
   static_assert(kQBytes <= kBufBytes, "q0 fits in a staging buffer");
   static constexpr int kOffG = kStages * kBufBytes;         // G [i][j]
-  static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;  // (d^-1, p, rho~ step^2, LLR level scale)
+  // floats per G row: the real run, the imaginary run and 4 floats of pad,
+  // so that consecutive rows start 16 bytes apart in bank position
+  static constexpr int kGRow = 2 * kUsers + 4;
+  static constexpr int kOffPre = kOffG + 4 * kUsers * kGRow;  // (d^-1, p, rho~ step^2, LLR level scale)
   static constexpr int kOffBar = kOffPre + 16 * kUsers;
   static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
   static constexpr int kThreads = 32;                       // one warp per CTA
   static_assert(kBufBytes % 1024 == 0, "swizzled boxes need 1024-byte alignment");
 };
 
-// G in shared memory, row i as [Re G_i0 .. Re G_i(NU-1) | Im G_i0 .. Im G_i(NU-1)]:
+// G in shared memory, row i as [Re G_i0 .. Re G_i(NU-1) | Im G_i0 .. Im G_i(NU-1) | pad]:
 // a sweep lane reads the real and the imaginary parts of its users as
 // separate runs (16-byte aligned for 4 consecutive users).
-__device__ __forceinline__ int wide_gre(int i, int j) { return i * 2 * WideShape::kUsers + j; }
+__device__ __forceinline__ int wide_gre(int i, int j) { return i * WideShape::kGRow + j; }
 __device__ __forceinline__ int wide_gim(int i, int j) {
-  return i * 2 * WideShape::kUsers + WideShape::kUsers + j;
+  return i * WideShape::kGRow + WideShape::kUsers + j;
 }
 // Fault word of the wide kernels (bit 0: a wait timed out; bit 1: a batched
 // cell's tensor map was misaligned).  Defined here because exactly one
@@ -108,6 +111,185 @@ __device__ __forceinline__ void mma2_round2(float (&d)[2][4], const uint32_t (&a
   mma_tf32(d[1], al[0], al[1], al[2], bh0, bh1);
 }
 
+// K sweeps on q (q0 in sq [symbol][user] on entry, z on exit) and the
+// outputs of symbols tb .. tb + np - 1 of subcarrier sc, by one warp:
+// lane = 2 ts + hf owns users [hf*16, hf*16 + 16) of symbol ts.  G is in sg
+// (wide_gre / wide_gim rows), (d^-1, p, rho~ step^2, LLR level scale) per
+// user in spre.  Shared by the warp-level and the tcgen05 32-user kernels.
+__device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float* sq,
+                                                    const float* sg, const float* spre,
+                                                    long long sc, int tb, int np) {
+  constexpr int UP = WideShape::kUP;
+  constexpr int NU = WideShape::kUsers;
+  const int lane = threadIdx.x & 31;
+  const int U = P.U;
+  const int T = P.T;
+#if OCD_WIDE_F32X2
+  {
+    // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts; q as
+    // packed pairs of consecutive users, updated with fma.rn.f32x2 (each
+    // half one IEEE fma: the same operations, in the same order, as the
+    // scalar form)
+    const int ts = lane >> 1;
+    const int hf = lane & 1;
+    const bool act = ts < np;
+    unsigned long long QR[UP / 2], QI[UP / 2];
+    float zr[UP], zi[UP];
+#pragma unroll
+    for (int l2 = 0; l2 < UP / 2; ++l2) {
+      const int j = hf * UP + 2 * l2;
+      QR[l2] = act ? f2_pack(sq[2 * (ts * NU + j)], sq[2 * (ts * NU + j + 1)]) : 0ull;
+      QI[l2] = act ? f2_pack(sq[2 * (ts * NU + j) + 1], sq[2 * (ts * NU + j + 1) + 1]) : 0ull;
+      zr[2 * l2] = zr[2 * l2 + 1] = 0.0f;
+      zi[2 * l2] = zi[2 * l2 + 1] = 0.0f;
+    }
+    const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
+    const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
+    for (int k = 0; k < P.K; ++k) {
+#pragma unroll 1
+      for (int oh = 0; oh < 2; ++oh) {
+#pragma unroll
+      for (int lu = 0; lu < UP; ++lu) {
+        const int u = oh * UP + lu;
+        if (u < U) {
+          const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
+          float q0, q1, p0, p1;
+          f2_unpack(QR[lu >> 1], q0, q1);
+          f2_unpack(QI[lu >> 1], p0, p1);
+          const float qr = (lu & 1) ? q1 : q0;
+          const float qi = (lu & 1) ? p1 : p0;
+          float wr = fmaf(dp.x, qr, dp.y * zr[lu]);
+          float wi = fmaf(dp.x, qi, dp.y * zi[lu]);
+          wr = fminf(fmaxf(wr, -are), are);
+          wi = fminf(fmaxf(wi, -aim), aim);
+          const float dr0 = wr - zr[lu];
+          const float di0 = wi - zi[lu];
+          if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+          const int owner = (lane & ~1) | oh;
+          const float dr = __shfl_sync(kFullMask, dr0, owner);
+          const float di = __shfl_sync(kFullMask, di0, owner);
+          const unsigned long long DR = f2_pack(dr, dr);
+          const unsigned long long NDR = f2_pack(-dr, -dr);
+          const unsigned long long NDI = f2_pack(-di, -di);
+          const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
+          const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
+#pragma unroll
+          for (int l4 = 0; l4 < UP / 4; ++l4) {
+            const float4 r4 = gre[l4], i4 = gim[l4];
+            const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
+            const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
+            // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
+            f2_fma(QR[2 * l4], im0, NDI);
+            f2_fma(QR[2 * l4], re0, NDR);
+            f2_fma(QI[2 * l4], im0, DR);
+            f2_fma(QI[2 * l4], re0, NDI);
+            f2_fma(QR[2 * l4 + 1], im1, NDI);
+            f2_fma(QR[2 * l4 + 1], re1, NDR);
+            f2_fma(QI[2 * l4 + 1], im1, DR);
+            f2_fma(QI[2 * l4 + 1], re1, NDI);
+          }
+        }
+      }
+      }
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int l = 0; l < UP; ++l) {
+        const int j = hf * UP + l;
+        sq[2 * (ts * NU + j)] = zr[l];
+        sq[2 * (ts * NU + j) + 1] = zi[l];
+      }
+    }
+    __syncwarp();
+  }
+#else
+  {
+    // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts
+    const int ts = lane >> 1;
+    const int hf = lane & 1;
+    const bool act = ts < np;
+    float qr[UP], qi[UP], zr[UP], zi[UP];
+#pragma unroll
+    for (int l = 0; l < UP; ++l) {
+      const int j = hf * UP + l;
+      qr[l] = act ? sq[2 * (ts * NU + j)] : 0.0f;
+      qi[l] = act ? sq[2 * (ts * NU + j) + 1] : 0.0f;
+      zr[l] = 0.0f;
+      zi[l] = 0.0f;
+    }
+    const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
+    const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
+    for (int k = 0; k < P.K; ++k) {
+      // users in two halves of UP (the owner half oh is a loop variable,
+      // the slot lu a compile-time index): half the code of a full unroll
+#pragma unroll 1
+      for (int oh = 0; oh < 2; ++oh) {
+#pragma unroll
+      for (int lu = 0; lu < UP; ++lu) {
+        const int u = oh * UP + lu;
+        if (u < U) {
+          const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
+          float wr = fmaf(dp.x, qr[lu], dp.y * zr[lu]);
+          float wi = fmaf(dp.x, qi[lu], dp.y * zi[lu]);
+          wr = fminf(fmaxf(wr, -are), are);
+          wi = fminf(fmaxf(wi, -aim), aim);
+          const float dr0 = wr - zr[lu];
+          const float di0 = wi - zi[lu];
+          if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+          const int owner = (lane & ~1) | oh;
+          const float dr = __shfl_sync(kFullMask, dr0, owner);
+          const float di = __shfl_sync(kFullMask, di0, owner);
+          const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
+          const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
+#pragma unroll
+          for (int l4 = 0; l4 < UP / 4; ++l4) {
+            const float4 r4 = gre[l4], i4 = gim[l4];
+            const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int l = 4 * l4 + c;
+              qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
+              qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
+            }
+          }
+        }
+      }
+      }
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int l = 0; l < UP; ++l) {
+        const int j = hf * UP + l;
+        sq[2 * (ts * NU + j)] = zr[l];
+        sq[2 * (ts * NU + j) + 1] = zi[l];
+      }
+    }
+    __syncwarp();
+  }
+#endif
+  for (int f = lane; f < np * U; f += 32) {
+    const int ts = f / U;
+    const int u = f - ts * U;
+    const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
+    const long long o = (sc * T + tb + ts) * U + u;
+    if (P.xhat) P.xhat[o] = z;
+    if (P.llr) {
+      float* out = P.llr + o * P.Q;
+      const float inv = spre[4 * u + 3];
+      if (!(inv > 0.0f)) {
+        for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
+      } else {
+        const float rs2 = spre[4 * u + 2];
+        dimension_llr(z.x * inv, rs2, P, out);
+        if (!P.bpsk) dimension_llr(z.y * inv, rs2, P, out + P.nb);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // One warp's walk over subcarriers first, first + stride, ... (< end) of
 // problem P (ymap: Y as [Nsc*T][2B] floats, box 32 x 16, 128-byte swizzle).
 // Staging area and barriers persist across calls as in tma_walk; returns
@@ -118,7 +300,6 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
                                           long long first, long long end, long long stride) {
   using S = WideShape;
   constexpr int BB = S::kBB;
-  constexpr int UP = S::kUP;
   constexpr int NU = S::kUsers;
   const int lane = threadIdx.x & 31;
   float* sg = reinterpret_cast<float*>(ws + S::kOffG);
@@ -386,170 +567,7 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
           sq[2 * (ts * NU + u) + 1] = a[1][2 + e] + a[0][2 + e];
         }
     __syncwarp();
-#if OCD_WIDE_F32X2
-    {
-      // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts; q as
-      // packed pairs of consecutive users, updated with fma.rn.f32x2 (each
-      // half one IEEE fma: the same operations, in the same order, as the
-      // scalar form)
-      const int ts = lane >> 1;
-      const int hf = lane & 1;
-      const bool act = ts < np;
-      unsigned long long QR[UP / 2], QI[UP / 2];
-      float zr[UP], zi[UP];
-#pragma unroll
-      for (int l2 = 0; l2 < UP / 2; ++l2) {
-        const int j = hf * UP + 2 * l2;
-        QR[l2] = act ? f2_pack(sq[2 * (ts * NU + j)], sq[2 * (ts * NU + j + 1)]) : 0ull;
-        QI[l2] = act ? f2_pack(sq[2 * (ts * NU + j) + 1], sq[2 * (ts * NU + j + 1) + 1]) : 0ull;
-        zr[2 * l2] = zr[2 * l2 + 1] = 0.0f;
-        zi[2 * l2] = zi[2 * l2 + 1] = 0.0f;
-      }
-      const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
-      const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
-      for (int k = 0; k < P.K; ++k) {
-#pragma unroll 1
-        for (int oh = 0; oh < 2; ++oh) {
-#pragma unroll
-        for (int lu = 0; lu < UP; ++lu) {
-          const int u = oh * UP + lu;
-          if (u < U) {
-            const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
-            float q0, q1, p0, p1;
-            f2_unpack(QR[lu >> 1], q0, q1);
-            f2_unpack(QI[lu >> 1], p0, p1);
-            const float qr = (lu & 1) ? q1 : q0;
-            const float qi = (lu & 1) ? p1 : p0;
-            float wr = fmaf(dp.x, qr, dp.y * zr[lu]);
-            float wi = fmaf(dp.x, qi, dp.y * zi[lu]);
-            wr = fminf(fmaxf(wr, -are), are);
-            wi = fminf(fmaxf(wi, -aim), aim);
-            const float dr0 = wr - zr[lu];
-            const float di0 = wi - zi[lu];
-            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
-            const int owner = (lane & ~1) | oh;
-            const float dr = __shfl_sync(kFullMask, dr0, owner);
-            const float di = __shfl_sync(kFullMask, di0, owner);
-            const unsigned long long DR = f2_pack(dr, dr);
-            const unsigned long long NDR = f2_pack(-dr, -dr);
-            const unsigned long long NDI = f2_pack(-di, -di);
-            const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
-            const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
-#pragma unroll
-            for (int l4 = 0; l4 < UP / 4; ++l4) {
-              const float4 r4 = gre[l4], i4 = gim[l4];
-              const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
-              const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
-              // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
-              f2_fma(QR[2 * l4], im0, NDI);
-              f2_fma(QR[2 * l4], re0, NDR);
-              f2_fma(QI[2 * l4], im0, DR);
-              f2_fma(QI[2 * l4], re0, NDI);
-              f2_fma(QR[2 * l4 + 1], im1, NDI);
-              f2_fma(QR[2 * l4 + 1], re1, NDR);
-              f2_fma(QI[2 * l4 + 1], im1, DR);
-              f2_fma(QI[2 * l4 + 1], re1, NDI);
-            }
-          }
-        }
-        }
-      }
-      __syncwarp();
-      if (act) {
-#pragma unroll
-        for (int l = 0; l < UP; ++l) {
-          const int j = hf * UP + l;
-          sq[2 * (ts * NU + j)] = zr[l];
-          sq[2 * (ts * NU + j) + 1] = zi[l];
-        }
-      }
-      __syncwarp();
-    }
-#else
-    {
-      // lane = 2 ts + hf holds users [hf*UP, hf*UP + UP) of symbol ts
-      const int ts = lane >> 1;
-      const int hf = lane & 1;
-      const bool act = ts < np;
-      float qr[UP], qi[UP], zr[UP], zi[UP];
-#pragma unroll
-      for (int l = 0; l < UP; ++l) {
-        const int j = hf * UP + l;
-        qr[l] = act ? sq[2 * (ts * NU + j)] : 0.0f;
-        qi[l] = act ? sq[2 * (ts * NU + j) + 1] : 0.0f;
-        zr[l] = 0.0f;
-        zi[l] = 0.0f;
-      }
-      const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
-      const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
-      for (int k = 0; k < P.K; ++k) {
-        // users in two halves of UP (the owner half oh is a loop variable,
-        // the slot lu a compile-time index): half the code of a full unroll
-#pragma unroll 1
-        for (int oh = 0; oh < 2; ++oh) {
-#pragma unroll
-        for (int lu = 0; lu < UP; ++lu) {
-          const int u = oh * UP + lu;
-          if (u < U) {
-            const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
-            float wr = fmaf(dp.x, qr[lu], dp.y * zr[lu]);
-            float wi = fmaf(dp.x, qi[lu], dp.y * zi[lu]);
-            wr = fminf(fmaxf(wr, -are), are);
-            wi = fminf(fmaxf(wi, -aim), aim);
-            const float dr0 = wr - zr[lu];
-            const float di0 = wi - zi[lu];
-            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
-            const int owner = (lane & ~1) | oh;
-            const float dr = __shfl_sync(kFullMask, dr0, owner);
-            const float di = __shfl_sync(kFullMask, di0, owner);
-            const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
-            const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
-#pragma unroll
-            for (int l4 = 0; l4 < UP / 4; ++l4) {
-              const float4 r4 = gre[l4], i4 = gim[l4];
-              const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int l = 4 * l4 + c;
-                qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
-                qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
-              }
-            }
-          }
-        }
-        }
-      }
-      __syncwarp();
-      if (act) {
-#pragma unroll
-        for (int l = 0; l < UP; ++l) {
-          const int j = hf * UP + l;
-          sq[2 * (ts * NU + j)] = zr[l];
-          sq[2 * (ts * NU + j) + 1] = zi[l];
-        }
-      }
-      __syncwarp();
-    }
-#endif
-    for (int f = lane; f < np * U; f += 32) {
-      const int ts = f / U;
-      const int u = f - ts * U;
-      const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
-      const long long o = (sc * T + tb + ts) * U + u;
-      if (P.xhat) P.xhat[o] = z;
-      if (P.llr) {
-        float* out = P.llr + o * P.Q;
-        const float inv = spre[4 * u + 3];
-        if (!(inv > 0.0f)) {
-          for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
-        } else {
-          const float rs2 = spre[4 * u + 2];
-          dimension_llr(z.x * inv, rs2, P, out);
-          if (!P.bpsk) dimension_llr(z.y * inv, rs2, P, out + P.nb);
-        }
-      }
-    }
-    __syncwarp();
+    wide_sweeps_outputs(P, sq, sg, spre, sc, tb, np);
   }
   return true;
 }
