@@ -30,10 +30,11 @@
 //   warp 1      one thread issues 3 MMAs per K slice of 8 into the
 //               subcarrier's TMEM slot and commits each block (the stage is
 //               free again) and each subcarrier (accumulators ready);
-//   warps 6-9   epilogue, one per TMEM lane quarter: groups of 4 subcarriers
-//               are drained from TMEM together (an M = 64 accumulator keeps
-//               row 16q + i in lane 32q + i), then each warp runs the
-//               preprocessing, the K sweeps and the outputs of one of them.
+//   warps 6-13  epilogue, two per TMEM lane quarter: groups of 8 subcarriers
+//               (4 pairs, every TMEM slot) are drained from TMEM (rows 32q ..
+//               32q + 31 of an M = 128 accumulator sit in lane quarter q),
+//               each slot released as soon as it is read; then each warp runs
+//               the preprocessing, the K sweeps and the outputs of one of them.
 // Eight TMEM slots of 64 columns (two groups of four) let the MMAs of one
 // group run under the epilogue of the previous one.  Every wait is bounded
 // in wall time; a wait that expires sets the fault word and a shared abort
@@ -47,7 +48,7 @@
 namespace ocd {
 
 #ifndef OCD_TC_RAW_STAGES
-#define OCD_TC_RAW_STAGES 6   // pair blocks whose copies may be in flight (72 KB per SM)
+#define OCD_TC_RAW_STAGES 3   // pair blocks whose copies may be in flight (36 KB per SM)
 #endif
 #ifndef OCD_TC_OP_STAGES
 #define OCD_TC_OP_STAGES 2    // operand buffers (transform ahead of the MMAs)
@@ -80,19 +81,32 @@ struct TcShape {
   static constexpr int kEpiQ = 16 * 32 * 8;               // q0, then z, [symbol][user]
   static constexpr int kEpiPre = 32 * 16;                 // (d^-1, p, rho~ step^2, u scale)
   static constexpr int kEpiBytes = kEpiG + kEpiQ + kEpiPre;
+  static constexpr int kEpiWarps = 8;                     // one subcarrier each per group
   static constexpr int kOffRaw = kOpStages * kOpStageBytes;
   static constexpr int kOffEpi = kOffRaw + kRawStages * kRawStageBytes;
-  static constexpr int kOffBar = kOffEpi + 4 * kEpiBytes;
+  static constexpr int kOffBar = kOffEpi + kEpiWarps * kEpiBytes;
   static constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 * kSlots;
   static constexpr int kOffTmem = kOffBar + 8 * kNumBars;
   static constexpr int kOffAbort = kOffTmem + 4;
   static constexpr int kBytes = kOffAbort + 4;
-  static constexpr int kTransformWarps = 8;
-  static constexpr int kThreads = 32 * (2 + kTransformWarps + 4);  // 448
+  static constexpr int kTransformWarps = 4;
+  static constexpr int kThreads = 32 * (2 + kTransformWarps + kEpiWarps);  // 448
+  static_assert(kEpiWarps == 2 * kSlots, "a group of subcarriers fills the TMEM slots");
   static_assert(kOpBytes % 1024 == 0 && kRawY % 1024 == 0 && kRawStageBytes % 1024 == 0,
                 "1024-byte swizzle phase");
   static_assert(kN <= kSlotCols && kN % 16 == 0, "one pair's accumulators fit a slot");
 };
+
+// Cycle counters per role (waits and work), compiled in only with
+// OCD_TC_TRACE: four per warp, summed over the CTAs into g_tc_trace.
+#ifdef OCD_TC_TRACE
+__device__ unsigned long long g_tc_trace[16 * 4];
+#define TC_CLOCK(v) const long long v = clock64()
+#define TC_ADD(k, v) tr[k] += (unsigned long long)(clock64() - v)
+#else
+#define TC_CLOCK(v)
+#define TC_ADD(k, v)
+#endif
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -101,14 +115,31 @@ __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// mbarrier try-wait that lets the thread sleep until the phase completes or
+// about `hint_ns` have passed (no issue slots spent while it sleeps).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait that also gives up when another role has aborted; an expired
-// limit sets the abort flag and bit 0 of the fault word.
+// limit sets the abort flag and bit 0 of the fault word.  Between checks the
+// thread sleeps on the barrier (up to 20 us), so waiting roles leave the
+// issue slots to the working ones.
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns,
                                         volatile int* abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
     if (*abort_flag) return false;
     if (global_ns() - t0 >= limit_ns) {
       *abort_flag = 1;
@@ -189,6 +220,9 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(base + S::kOffTmem);
+#ifdef OCD_TC_TRACE
+  unsigned long long tr[4] = {0, 0, 0, 0};
+#endif
 
   if (warp == 0) {
     // ---------------- producer -------------------------------------------
@@ -202,10 +236,12 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
         for (int blk = 0; blk < nblk; ++blk, ++g) {
           const int st = (int)(g % R);
           const long long n = g / R;
+          TC_CLOCK(c0);
           if (n > 0 && !tc_wait(bar_free(st), (uint32_t)((n - 1) & 1), P.wait_ns, abort_flag)) {
             ok = false;
             break;
           }
+          TC_ADD(0, c0);
           const int b0 = blk * S::kBA;
           const int bb = min(S::kBA, B - b0);
           const uint32_t hbytes = (uint32_t)(bb * U * 8);
@@ -238,18 +274,23 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
       for (long long p = 0; p < npairs && ok; ++p) {
         const int slot = (int)(p % S::kSlots);
         const long long m = p / S::kSlots;
+        TC_CLOCK(c0);
         if (m > 0 && !tc_wait(bar_accempty(slot), (uint32_t)((m - 1) & 1), P.wait_ns, abort_flag)) {
           ok = false;
           break;
         }
+        TC_ADD(0, c0);
         tc_fence_after();
         const uint32_t d = tbase + (uint32_t)(slot * S::kSlotCols);
         for (int blk = 0; blk < nblk; ++blk, ++g) {
           const int st = (int)(g % O);
+          TC_CLOCK(c1);
           if (!tc_wait(bar_ready(st), (uint32_t)((g / O) & 1), P.wait_ns, abort_flag)) {
             ok = false;
             break;
           }
+          TC_ADD(1, c1);
+          TC_CLOCK(c2);
           tc_fence_after();
           // descriptors of the stage; the K slices are 32 bytes (2 units of
           // the start-address field) apart
@@ -268,6 +309,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
             tc_mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
           }
           tc_commit(bar_empty(st));
+          TC_ADD(2, c2);
         }
         if (!ok) break;
         tc_commit(bar_accfull(slot));
@@ -286,12 +328,20 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
       for (int blk = 0; blk < nblk; ++blk, ++g) {
         const int rs = (int)(g % R);
         const int os = (int)(g % O);
-        if (!tc_wait_warp(bar_full(rs), (uint32_t)((g / R) & 1), P.wait_ns, abort_flag) ||
-            (g >= O && !tc_wait_warp(bar_empty(os), (uint32_t)((g / O - 1) & 1), P.wait_ns,
-                                     abort_flag))) {
+        TC_CLOCK(c0);
+        if (!tc_wait_warp(bar_full(rs), (uint32_t)((g / R) & 1), P.wait_ns, abort_flag)) {
           ok = false;
           break;
         }
+        TC_ADD(0, c0);
+        TC_CLOCK(c1);
+        if (g >= O && !tc_wait_warp(bar_empty(os), (uint32_t)((g / O - 1) & 1), P.wait_ns,
+                                    abort_flag)) {
+          ok = false;
+          break;
+        }
+        TC_ADD(1, c1);
+        TC_CLOCK(c2);
         const int bb = min(S::kBA, B - blk * S::kBA);
         unsigned char* hi = base + os * S::kOpStageBytes;
         unsigned char* lo = hi + S::kOpBytes;
@@ -335,29 +385,35 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
           mbar_arrive(bar_free(rs));
           mbar_arrive(bar_ready(os));
         }
+        TC_ADD(2, c2);
       }
     }
   } else {
     // ---------------- epilogue --------------------------------------------
     // TMEM lane quarter q = rows 32q .. 32q + 31: Re_a, Re_b, Im_a, Im_b;
-    // lane = user
+    // lane = user.  Two warps per quarter: warp ew drains the pairs jp with
+    // jp % 2 == ew / 4 of a group of kSlots pairs, and finishes member ew.
+    constexpr int NEW = S::kEpiWarps;
     const int q = warp & 3;
-    const int ew = warp - EW0;                   // member of a group this warp finishes
+    const int ew = warp - EW0;
     const int half = q & 1;
     const int part = q >> 1;                     // 0: real parts, 1: imaginary parts
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const int cq = half * YR;                    // this warp's q0 columns
     const int cg = 2 * YR + 32 * half;           // this warp's G columns
-    // groups of two pairs (four subcarriers, one per epilogue warp)
-    for (long long p0 = 0; p0 < npairs; p0 += 2) {
-      named_bar_sync(1, 128);  // every member's buffers are free
-      for (int jp = 0; jp < 2; ++jp) {
+    for (long long p0 = 0; p0 < npairs; p0 += S::kSlots) {
+      TC_CLOCK(c0);
+      named_bar_sync(1, 32 * NEW);  // every member's buffers are free
+      TC_ADD(1, c0);
+      for (int jp = ew >> 2; jp < S::kSlots; jp += 2) {
         const long long p = p0 + jp;
         if (p >= npairs) break;
         const int slot = (int)(p % S::kSlots);
+        TC_CLOCK(c1);
         if (!tc_wait_warp(bar_accfull(slot), (uint32_t)((p / S::kSlots) & 1), P.wait_ns,
                           abort_flag))
           continue;  // aborted: skip the work, keep the barriers in step
+        TC_ADD(0, c1);
         tc_fence_after();
         uint32_t vq[16], vg0[16], vg1[16];
         const uint32_t ta = tbase + lane_base + (uint32_t)(slot * S::kSlotCols);
@@ -386,7 +442,10 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
                                    __uint_as_float(vg1[4 * c + 2]), __uint_as_float(vg1[4 * c + 3]));
         }
       }
-      named_bar_sync(1, 128);  // every member's G and q0 are in shared memory
+      TC_CLOCK(c2);
+      named_bar_sync(1, 32 * NEW);  // every member's G and q0 are in shared memory
+      TC_ADD(1, c2);
+      TC_CLOCK(c3);
       const long long i = 2 * p0 + ew;  // member ew: pair p0 + ew / 2, half ew % 2
       if (i < nitems && !*abort_flag) {
         unsigned char* eb = base + S::kOffEpi + ew * S::kEpiBytes;
@@ -408,8 +467,13 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
         __syncwarp();
         wide_sweeps_outputs(P, sq, sg, spre, first + i * stride, 0, T);
       }
+      TC_ADD(2, c3);
     }
   }
+#ifdef OCD_TC_TRACE
+  if (lane == 0)
+    for (int k = 0; k < 4; ++k) atomicAdd(&g_tc_trace[4 * warp + k], tr[k]);
+#endif
 
   tc_fence_before();
   __syncthreads();

@@ -111,6 +111,60 @@ __device__ __forceinline__ void mma2_round2(float (&d)[2][4], const uint32_t (&a
   mma_tf32(d[1], al[0], al[1], al[2], bh0, bh1);
 }
 
+// Outputs of symbols ts0 .. ts0 + ns - 1 of the pass starting at symbol tb of
+// subcarrier sc (z in sq [symbol][user], soft-output constants in spre), one
+// item per (symbol, user) and lane: a full set of 32 users splits the item
+// index with a shift, and the LLR code is chosen once by the bits per real
+// dimension (both dimensions' LLRs stored as float2 pairs when the array is
+// 8-byte aligned).
+__device__ __forceinline__ void wide_outputs(const DetectParams& P, const float* sq,
+                                             const float* spre, long long sc, int tb, int ts0,
+                                             int ns) {
+  constexpr int NU = WideShape::kUsers;
+  const int lane = threadIdx.x & 31;
+  const int U = P.U;
+  const int T = P.T;
+  auto outputs = [&](auto nbc) {
+    constexpr int NB = decltype(nbc)::value;
+    const bool full = U == NU;
+    const bool pairs = !P.bpsk && (reinterpret_cast<uintptr_t>(P.llr) & 7u) == 0;
+    for (int f = lane; f < ns * U; f += 32) {
+      const int ts = ts0 + (full ? f >> 5 : f / U);
+      const int u = f - (ts - ts0) * U;
+      const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
+      const long long o = (sc * T + tb + ts) * U + u;
+      if (P.xhat) P.xhat[o] = z;
+      if (P.llr) {
+        float* out = P.llr + o * P.Q;
+        const float inv = spre[4 * u + 3];
+        if (!(inv > 0.0f)) {
+          for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
+        } else {
+          const float rs2 = spre[4 * u + 2];
+          if (pairs) {
+            float L[2 * NB];
+            dimension_llr_nb<NB>(z.x * inv, rs2, L);
+            dimension_llr_nb<NB>(z.y * inv, rs2, L + NB);
+#pragma unroll
+            for (int j = 0; j < 2 * NB; j += 2)
+              *reinterpret_cast<float2*>(out + j) = make_float2(L[j], L[j + 1]);
+          } else {
+            dimension_llr_nb<NB>(z.x * inv, rs2, out);
+            if (!P.bpsk) dimension_llr_nb<NB>(z.y * inv, rs2, out + NB);
+          }
+        }
+      }
+    }
+  };
+  switch (P.nb) {
+    case 1: outputs(std::integral_constant<int, 1>{}); break;
+    case 2: outputs(std::integral_constant<int, 2>{}); break;
+    case 3: outputs(std::integral_constant<int, 3>{}); break;
+    default: outputs(std::integral_constant<int, 4>{}); break;
+  }
+  __syncwarp();
+}
+
 // K sweeps on q (q0 in sq [symbol][user] on entry, z on exit) and the
 // outputs of symbols tb .. tb + np - 1 of subcarrier sc, by one warp:
 // lane = 2 ts + hf owns users [hf*16, hf*16 + 16) of symbol ts.  G is in sg
@@ -269,25 +323,7 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
     __syncwarp();
   }
 #endif
-  for (int f = lane; f < np * U; f += 32) {
-    const int ts = f / U;
-    const int u = f - ts * U;
-    const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
-    const long long o = (sc * T + tb + ts) * U + u;
-    if (P.xhat) P.xhat[o] = z;
-    if (P.llr) {
-      float* out = P.llr + o * P.Q;
-      const float inv = spre[4 * u + 3];
-      if (!(inv > 0.0f)) {
-        for (int j = 0; j < P.Q; ++j) out[j] = 0.0f;
-      } else {
-        const float rs2 = spre[4 * u + 2];
-        dimension_llr(z.x * inv, rs2, P, out);
-        if (!P.bpsk) dimension_llr(z.y * inv, rs2, P, out + P.nb);
-      }
-    }
-  }
-  __syncwarp();
+  wide_outputs(P, sq, spre, sc, tb, 0, np);
 }
 
 // One warp's walk over subcarriers first, first + stride, ... (< end) of
