@@ -513,6 +513,7 @@ def run_ours(args):
             line["batched_form"] = form_summary(measure_batched, args)
             line["unfolded_form"] = form_summary(measure_unfolded, args)
             line["single_symbol_form"] = form_summary(measure_single, args)
+            line["wide_form"] = form_summary(measure_wide, args)
         print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         dist.barrier()
@@ -668,6 +669,72 @@ def run_single(args):
             "config": {"workload": "OCD-BOX T=1 K=3: 128x8 64-QAM and 32x8 16-QAM",
                        "l2": "inputs larger than L2 (no flush)"},
             "forms": res["forms"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+WIDE_CONFIGS = (  # (B, U, T, K, order, subcarriers per step)
+    (256, 32, 14, 4, 64, 4000),
+    (128, 32, 14, 3, 64, 8000),
+)
+
+
+def measure_wide(args):
+    """The projected form for 17-32 users (OCD-BOX at 15 dB): the
+    tensor-memory (tcgen05) kernel against the warp-level MMA kernel on the
+    same inputs (434 MB and 491 MB of algorithmic traffic per launch, inputs
+    larger than L2), each against the HBM
+    roofline of its algorithmic bytes."""
+    import torch
+
+    import paper_1611_08779_gb300 as ocd
+    from paper_1611_08779_gb300 import synth
+    dev = torch.device("cuda", 0)
+    peak = float(measured_peaks()[0].get("hbm_gbs", FALLBACK_HBM_GBS))
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    for b, u, t, k, order, nsc in WIDE_CONFIGS:
+        q = int(round(math.log2(order)))
+        d = synth.make_uplink(nsc, b, u, t, order, SNR_DB, seed=23)
+        H = torch.from_numpy(d["H"]).to(dev)
+        Y = torch.from_numpy(d["Y"]).to(dev)
+        del d["H"], d["Y"]
+        x = torch.empty((nsc, t, u), dtype=torch.complex64, device=dev)
+        llr = torch.empty((nsc, t, u, q), dtype=torch.float32, device=dev)
+        nbytes = algorithmic_bytes_per_sc(b, u, t, q) * nsc
+        row = []
+        for algo in ("projected_tc", "projected_warp"):
+            def step():
+                ocd.ocd_detect(H, Y, d["N0"], 1.0, k, args.mode, order, xhat=x, llr=llr,
+                               algo=algo, stream=stream)
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    step()
+            torch.cuda.synchronize(dev)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                for _ in range(args.steps):
+                    step()
+                ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            row += [nsc * t * u * q / (ms / 1e3) / 1e9, nbytes / (ms / 1e3) / 1e9 / peak, ms]
+        out[f"{b}x{u}_t{t}_k{k}"] = row
+        del H, Y, x, llr
+    return {"metric": "detected Gb/s, 17-32 users", "forms": out,
+            "summary": {"unit": "[tcgen05 Gb/s, hbm frac, ms, warp-level Gb/s, hbm frac, ms]",
+                        **out}}
+
+
+def run_wide(args):
+    res = measure_wide(args)
+    line = {"metric": res["metric"], "workload": "wide", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "OCD-BOX 256x32 T=14 K=4 and 128x32 T=14 K=3, 64-QAM",
+                       "l2": "inputs larger than L2 (no flush)"},
+            "forms": res["summary"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -907,13 +974,15 @@ def parser():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and unfolded forms in the headline line")
-    ap.add_argument("--workload", choices=["metric", "precision", "batched", "unfolded", "single"],
+    ap.add_argument("--workload", choices=["metric", "precision", "batched", "unfolded", "single",
+                                           "wide"],
                     default="metric",
                     help="metric: the headline 128x8 configuration; precision: 256x16 K=4 in "
                          "float32 / bfloat16 / float16 storage with per-SNR accuracy; batched: "
                          "mixed cells in one persistent launch; unfolded: differentiable OCD-BOX "
                          "forward + adjoint (128x16, K=5, 4096 samples); single: one symbol per "
-                         "channel (T=1: 128x8 64-QAM, 32x8 16-QAM)")
+                         "channel (T=1: 128x8 64-QAM, 32x8 16-QAM); wide: 17-32 users "
+                         "(tcgen05 and warp-level kernels)")
     ap.add_argument("--cells", type=int, default=24, help="cells of the batched workload")
     ap.add_argument("--clock-window", type=float, default=MIN_CLOCK_WINDOW_S,
                     help="seconds of clock sampling the timed steps are extended to")
@@ -935,6 +1004,8 @@ def main(argv=None):
         return run_unfolded(args)
     if args.workload == "single":
         return run_single(args)
+    if args.workload == "wide":
+        return run_wide(args)
     return run_ours(args)
 
 

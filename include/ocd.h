@@ -74,7 +74,7 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *   OCD_ALGO_PROJECTED_TC    the projected form with the tensor-memory kernel
  *                       for any shape it supports (16 < U <= 32, T <= 16, the
  *                       storage and alignment above); OCD_ERR_UNSUPPORTED
- *                       otherwise.  Not available in the batched form.
+ *                       otherwise.
  * All projected kernels give the same results up to FP32 rounding.
  */
 typedef enum {
@@ -193,15 +193,18 @@ int ocd_wait_selftest(int limit_us, cudaStream_t stream);
  * problems with different B, U, Nsc, T, K, mode and alphabet.  The batched
  * entry points detect a list of such problems ("cells") with persistent
  * kernels that draw their work from device ticket counters (atomicAdd only;
- * no kernel waits on another block).  Each cell's results are those of
- * ocd_detect_typed with the same arguments in the same arrangement.
+ * no kernel waits on another block); cells with 17-32 users and 9-16 symbols
+ * in the projected form run the tensor-memory kernel in a launch of their own.
+ * Each cell's results are those of ocd_detect_typed with the same arguments
+ * in the same arrangement.
  * ------------------------------------------------------------------------- */
 
 /* One cell: the arguments of ocd_detect_typed.  `algo` (ocd_algo_t):
  * OCD_ALGO_AUTO takes the tune table's choice for the cell's shape, else the
  * default (PROJECTED for float32 storage, U <= 32, even B and 16-byte
  * aligned H and Y, at any T; else RESIDUAL).  The batched PROJECTED form
- * needs exactly those conditions (OCD_ERR_UNSUPPORTED otherwise). */
+ * needs exactly those conditions (OCD_ERR_UNSUPPORTED otherwise);
+ * PROJECTED_WARP and PROJECTED_TC choose its kernels as for ocd_detect_ex. */
 typedef struct {
   const void* H;
   const void* Y;

@@ -41,7 +41,8 @@ constexpr int kDefaultStepsPerTicket = 8;  // bulk-copy form: staged steps per t
 
 struct CellPlan {
   int index;              // position in the caller's list
-  int kind;               // 0 residual, 1 bulk-copy projected, 2 one lane per subcarrier
+  int kind;               // 0 residual, 1 bulk-copy projected, 2 one lane per subcarrier,
+                          // 3 tcgen05 projected (a one-cell launch)
   int npp, S, nt, ut;     // kernel instance
   bool fused;             // 32-user kernel with q0 in the G phase (T <= 8)
   size_t smem;
@@ -77,9 +78,12 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   const bool wide = can_wide(cp.P);
   const bool tma_ok = can_tma32(cp.P) || wide;
   int algo = c.algo;
-  if (algo == OCD_ALGO_PROJECTED_TC)
-    return fail(OCD_ERR_UNSUPPORTED, "cell %d: the batched form has no tcgen05 kernel", index);
-  if (algo == OCD_ALGO_PROJECTED_WARP) algo = OCD_ALGO_PROJECTED;  // the batched kernels are warp-level
+  if (algo == OCD_ALGO_PROJECTED_TC && !can_tc(cp.P))
+    return fail(OCD_ERR_UNSUPPORTED, "the tcgen05 kernel needs 16 < U <= 32, T <= %d, float32 "
+                "storage, even B and 16-byte aligned H and Y", ocd::kTcMaxSymbols);
+  const bool warp_only = algo == OCD_ALGO_PROJECTED_WARP;
+  const bool use_tc = algo == OCD_ALGO_PROJECTED_TC;
+  if (warp_only || use_tc) algo = OCD_ALGO_PROJECTED;
   if (algo == OCD_ALGO_AUTO && te && (te->algo == OCD_ALGO_RESIDUAL || te->algo == OCD_ALGO_PROJECTED))
     algo = te->algo;
   // default without a tune entry: the bulk-copy projected form wherever it
@@ -99,6 +103,19 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
     cp.sc_per_tick = 0;
     cp.tickets = 0;
     cp.work = (double)c.Nsc * (8.0 * c.B * c.U + 8.0 * c.B + 12.0 * c.U);
+    return OCD_OK;
+  }
+  if (algo == OCD_ALGO_PROJECTED && (use_tc || (!warp_only && prefer_tc(cp.P)))) {
+    // 17-32 users, 9-16 symbols: the single-problem path's tcgen05 kernel,
+    // launched for this cell alone (one CTA per SM, same results)
+    cp.kind = 3;
+    cp.ut = 4;
+    cp.npp = cp.S = 0;
+    cp.nt = ocd::projected_tc_threads();
+    cp.smem = ocd::projected_tc_smem_per_cta(c.T);
+    cp.sc_per_tick = 0;
+    cp.tickets = 0;
+    cp.work = (double)c.Nsc * (8.0 * c.B * c.U + 8.0 * c.T * c.B + 12.0 * c.T * c.U);
     return OCD_OK;
   }
   if (algo == OCD_ALGO_PROJECTED) {
@@ -156,6 +173,7 @@ struct Launch {
   std::unique_ptr<ocd::BatchTable> tab;  // persistent launches: the cell table
   bool single = false;                   // one-cell launch with parameters P
   ocd::DetectParams P;
+  std::unique_ptr<CUtensorMap> map;      // one-cell tcgen05 launch: its tensor map
 };
 
 // Plans every cell and groups them into launches (heaviest first).
@@ -193,6 +211,24 @@ int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
       if (st != OCD_OK) return st;
       if (L.grid == 0)
         return fail(OCD_ERR_UNSUPPORTED, "cell %d: one-lane kernel cannot be resident", plans[i].index);
+      launches.push_back(std::move(L));
+      continue;
+    }
+    if (plans[i].kind == 3) {
+      taken[i] = true;
+      Launch L;
+      L.single = true;
+      L.P = plans[i].P;
+      L.fn = ocd::projected_tc_kernel_ptr(plans[i].P.T);
+      L.nt = plans[i].nt;
+      L.smem = plans[i].smem;
+      L.work = plans[i].work;
+      L.map.reset(new CUtensorMap);
+      const cudaError_t e = ocd::encode_ymap_rows(L.P, L.map.get(), L.P.T <= 8 ? 8 : 16);
+      if (e == cudaErrorNotSupported)
+        return fail(OCD_ERR_UNSUPPORTED, "cell %d: no tensor-map encoder in this driver", plans[i].index);
+      if (e != cudaSuccess) return fail(OCD_ERR_CUDA, "cell %d: tensor map encoding failed", plans[i].index);
+      L.grid = (unsigned)std::min<long long>(di.sms, L.P.Nsc);  // one CTA per SM, persistent
       launches.push_back(std::move(L));
       continue;
     }
@@ -291,6 +327,10 @@ int enqueue(std::vector<Launch>& launches, void* workspace, cudaStream_t stream)
   // a persistent launch takes (cell table, its ticket counter); a one-cell
   // launch takes the cell's parameters
   auto launch = [&](Launch& L, unsigned int* ctr, cudaStream_t s) {
+    if (L.single && L.map) {
+      void* args[] = {&L.P, L.map.get()};
+      return cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, s);
+    }
     if (L.single) {
       void* args[] = {&L.P};
       return cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.nt), args, L.smem, s);

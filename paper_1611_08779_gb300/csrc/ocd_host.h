@@ -53,6 +53,8 @@ int make_plan(int B, int U, int T, size_t budget, ocd::DetectParams& P, Plan& pl
 bool can_tma32(const ocd::DetectParams& P);  // U <= 16
 bool can_lane(const ocd::DetectParams& P);   // T == 1, U <= 8: one lane per subcarrier
 bool can_wide(const ocd::DetectParams& P);   // 16 < U <= 32
+bool can_tc(const ocd::DetectParams& P);     // the tcgen05 kernel supports the shape
+bool prefer_tc(const ocd::DetectParams& P);  // ... and is the projected default
 
 // Grid of the one-lane-per-subcarrier kernel for P (0 when it cannot be
 // resident on the device).

@@ -48,17 +48,16 @@ def test_mixed_cells_match_the_oracle():
 
 @pytest.mark.parametrize("algo", ["residual", "projected"])
 def test_batched_is_bit_identical_to_the_single_problem_path(algo):
-    """Each cell equals ocd_detect in the arrangement the batched form runs:
-    the residual form, or the projected form with warp-level products (the
-    batched form has no tensor-memory kernel)."""
+    """Each cell equals ocd_detect in the same arrangement (the batched form
+    runs the single-problem kernels' per-subcarrier code, and the same
+    tensor-memory kernel for the cells with 17-32 users and 9-16 symbols)."""
     specs = [s for s in synth.mixed_cell_specs(16, seed=701, nsc_lo=20, nsc_hi=60)
              if algo == "residual" or s["B"] % 2 == 0]
     data, cells = build_cells(specs, algo=algo)
     ocd.ocd_detect_batched(cells)
     torch.cuda.synchronize()
-    single = "projected_warp" if algo == "projected" else algo
     for s, c in zip(specs, cells):
-        x, L = ocd.ocd_detect(c.H, c.Y, c.N0, 1.0, c.K, c.mode, c.qam_order, algo=single)
+        x, L = ocd.ocd_detect(c.H, c.Y, c.N0, 1.0, c.K, c.mode, c.qam_order, algo=algo)
         torch.cuda.synchronize()
         assert torch.equal(x, c.xhat), s
         assert torch.equal(L, c.llr), s
