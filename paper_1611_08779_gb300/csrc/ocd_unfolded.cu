@@ -461,10 +461,12 @@ __device__ __forceinline__ void qsweep(const UnfoldParams& P, const float2* sG, 
 // lo*hi; FP32-level accuracy).  A k-step covers antennas 4s + t (lane t of a
 // quad): A = [Re H^H; Im H^H] of user tile m, B = the same entries of user
 // tile n (G) or the received vector in column 0 (q0).  UT = user tiles.
-template <int UT, int NA>
-__device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float2* sG, int U,
-                                             int B, int lane) {
-  constexpr int st = staged_stride<NA>();
+// G = H^H H and q0 = H^H y (see gram_q0_tf32) from loaders hld(u, a) (user u,
+// antenna a; zero for u >= U is handled here, for a >= B by the loader) and
+// yld(a); q0 of user u goes to sq[u].
+template <int UT, class HL, class YL>
+__device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, float2* sG, int U,
+                                                  int B, int lane) {
   constexpr int NG = UT * (UT + 1) / 2;
   const int gq = lane >> 2, t = lane & 3;
   const int gst = U + 1;
@@ -477,46 +479,62 @@ __device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float
   for (int i = 0; i < UT; ++i)
 #pragma unroll
     for (int e = 0; e < 4; ++e) { qa[i][0][e] = 0.0f; qa[i][1][e] = 0.0f; }
+  // k-steps in chunks of KC: the loads of a chunk are issued before its
+  // products, so that they are in flight together (fewer k-steps per chunk
+  // for four user tiles, whose accumulators take most of the registers)
+  constexpr int KC = UT >= 4 ? 2 : 8;
   const int nks = (B + 3) / 4;
-  for (int ks = 0; ks < nks; ++ks) {
-    const int a = 4 * ks + t;  // < 32 NA: padding antennas hold zeros
-    uint32_t ah[UT][3], al[UT][3];
+  for (int ks0 = 0; ks0 < nks; ks0 += KC) {
+    const int nc = min(KC, nks - ks0);
+    float2 hv[KC][UT], yv[KC];
 #pragma unroll
-    for (int m = 0; m < UT; ++m) {
-      const int u = m * 8 + gq;
-      const float2 h = u < U ? sH[u * st + a] : make_float2(0.0f, 0.0f);
-      split_tf32(h.x, ah[m][0], al[m][0]);
-      split_tf32(h.y, ah[m][2], al[m][2]);
-      ah[m][1] = ah[m][2] ^ 0x80000000u;
-      al[m][1] = al[m][2] ^ 0x80000000u;
-    }
-    const float2 y = gq == 0 ? sy[a] : make_float2(0.0f, 0.0f);
-    uint32_t yh0, yl0, yh1, yl1;
-    split_tf32(y.x, yh0, yl0);
-    split_tf32(y.y, yh1, yl1);
-    // round 1: hi*hi and hi*lo of every tile (independent MMAs); round 2:
-    // lo*hi, added to a part round 1 updated several MMAs earlier
-    int tile = 0;
+    for (int c = 0; c < KC; ++c) {
+      const int a = 4 * (ks0 + c) + t;
 #pragma unroll
-    for (int m = 0; m < UT; ++m) {
-#pragma unroll
-      for (int n = m; n < UT; ++n, ++tile) {
-        mma_tf32(g[tile][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
-        mma_tf32(g[tile][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
+      for (int m = 0; m < UT; ++m) {
+        const int u = m * 8 + gq;
+        hv[c][m] = (c < nc && u < U) ? hld(u, a) : make_float2(0.0f, 0.0f);
       }
-      mma_tf32(qa[m][0], ah[m][0], ah[m][1], ah[m][2], yh0, yh1);
-      mma_tf32(qa[m][1], ah[m][0], ah[m][1], ah[m][2], yl0, yl1);
+      yv[c] = (c < nc && gq == 0) ? yld(a) : make_float2(0.0f, 0.0f);
     }
-    tile = 0;
 #pragma unroll
-    for (int m = 0; m < UT; ++m) {
+    for (int c = 0; c < KC; ++c) {
+      if (c >= nc) break;
+      uint32_t ah[UT][3], al[UT][3];
 #pragma unroll
-      for (int n = m; n < UT; ++n, ++tile)
-        mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
-      mma_tf32(qa[m][1], al[m][0], al[m][1], al[m][2], yh0, yh1);
+      for (int m = 0; m < UT; ++m) {
+        split_tf32(hv[c][m].x, ah[m][0], al[m][0]);
+        split_tf32(hv[c][m].y, ah[m][2], al[m][2]);
+        ah[m][1] = ah[m][2] ^ 0x80000000u;
+        al[m][1] = al[m][2] ^ 0x80000000u;
+      }
+      uint32_t yh0, yl0, yh1, yl1;
+      split_tf32(yv[c].x, yh0, yl0);
+      split_tf32(yv[c].y, yh1, yl1);
+      // round 1: hi*hi and hi*lo of every tile (independent MMAs); round 2:
+      // lo*hi, added to a part round 1 updated several MMAs earlier
+      int tile = 0;
+#pragma unroll
+      for (int m = 0; m < UT; ++m) {
+#pragma unroll
+        for (int n = m; n < UT; ++n, ++tile) {
+          mma_tf32(g[tile][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
+          mma_tf32(g[tile][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
+        }
+        mma_tf32(qa[m][0], ah[m][0], ah[m][1], ah[m][2], yh0, yh1);
+        mma_tf32(qa[m][1], ah[m][0], ah[m][1], ah[m][2], yl0, yl1);
+      }
+      tile = 0;
+#pragma unroll
+      for (int m = 0; m < UT; ++m) {
+#pragma unroll
+        for (int n = m; n < UT; ++n, ++tile)
+          mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
+        mma_tf32(qa[m][1], al[m][0], al[m][1], al[m][2], yh0, yh1);
+      }
     }
   }
-  __syncwarp();  // every lane's reads of sy are done before q0 overwrites it
+  __syncwarp();  // every lane's reads of y are done before q0 can overwrite it
   int tile = 0;
 #pragma unroll
   for (int m = 0; m < UT; ++m) {
@@ -536,8 +554,29 @@ __device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float
     }
     const int u = m * 8 + gq;
     if (t == 0 && u < U)  // column 0 holds q0: rows gq (re) and gq + 8 (im)
-      sy[u] = make_float2(qa[m][1][0] + qa[m][0][0], qa[m][1][2] + qa[m][0][2]);
+      sq[u] = make_float2(qa[m][1][0] + qa[m][0][0], qa[m][1][2] + qa[m][0][2]);
   }
+}
+
+template <int UT, int NA>
+__device__ __forceinline__ void gram_q0_tf32(const float2* sH, float2* sy, float2* sG, int U,
+                                             int B, int lane) {
+  constexpr int st = staged_stride<NA>();
+  gram_q0_tf32_impl<UT>(
+      [&](int u, int a) { return sH[u * st + a]; },  // antennas >= B hold zeros
+      [&](int a) { return sy[a]; }, sy, sG, U, B, lane);
+}
+
+// The same products with H and y read directly from global memory (the
+// sample's channel Hw [B][U] and received vector yw [B]); q0 goes to sq.
+// A k-step's channel loads cover 4 antenna rows x 8 consecutive users per
+// user tile: whole 32-byte sectors.
+template <int UT>
+__device__ __forceinline__ void gram_q0_tf32_global(const float2* Hw, const float2* yw, float2* sq,
+                                                    float2* sG, int U, int B, int lane) {
+  gram_q0_tf32_impl<UT>(
+      [&](int u, int a) { return a < B ? __ldg(Hw + (long long)a * U + u) : make_float2(0.0f, 0.0f); },
+      [&](int a) { return a < B ? __ldg(yw + a) : make_float2(0.0f, 0.0f); }, sq, sG, U, B, lane);
 }
 
 // UT: 8-user MMA tiles of the Gram product (1, 2 or 4); one instance each,
@@ -713,6 +752,235 @@ ocd_unfolded_proj_backward_kernel(const __grid_constant__ UnfoldParams P) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two samples per warp (U <= 16): lanes 0-15 carry sample 2i, lanes 16-31
+// sample 2i + 1, so that every lane of a user update works (one warp per
+// sample leaves half of them idle at U = 16).  Lane j = lane % 16 holds q_j,
+// z_j, ||h_j||^2 and their adjoints for its half's sample; shuffles stay in
+// the half (width 16) and sums run over it.  Per value the operations, and
+// the order of every sum, are those of the one-sample kernels above (there
+// the upper 16 lanes only ever added zeros), so the results are identical.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 shfl2_16(float2 v, int src) {
+  return make_float2(__shfl_sync(kFullMask, v.x, src, 16), __shfl_sync(kFullMask, v.y, src, 16));
+}
+__device__ __forceinline__ float half_sum(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+  return v;
+}
+
+// qsweep with the lane's half: j = lane % 16, sGh = the half's G.
+template <bool KEEP>
+__device__ __forceinline__ void qsweep16(const UnfoldParams& P, const float2* sGh, int gst, int j,
+                                         float2& q, float2& z, float d, float p, float om,
+                                         float2& zb, float2& qs) {
+  for (int u = 0; u < P.U; ++u) {
+    float wr = fmaf(d, q.x, p * z.x);
+    float wi = fmaf(d, q.y, p * z.y);
+    project(wr, wi, P.D);
+    const float2 dz = shfl2_16(make_float2(om * (wr - z.x), om * (wi - z.y)), u);
+    if (j == u) {
+      if (KEEP) {
+        zb = z;
+        qs = q;
+      }
+      z = make_float2(z.x + dz.x, z.y + dz.y);
+    }
+    const float2 g = j < P.U ? sGh[j * gst + u] : make_float2(0.0f, 0.0f);
+    q.x = fmaf(-g.x, dz.x, fmaf(g.y, dz.y, q.x));
+    q.y = fmaf(-g.x, dz.y, fmaf(-g.y, dz.x, q.y));
+  }
+}
+
+// Shared-memory words of one warp of the paired forward: q0 of the two
+// samples (32 each) and their two G.  The channel and the received vector
+// are read from global memory by the Gram products (each read once).
+__host__ __device__ inline int proj_pair_warp_elems(int U) { return 2 * 32 + 2 * U * (U + 1); }
+
+template <int UT>
+__global__ void __launch_bounds__(128)
+ocd_unfolded_proj_forward_pair_kernel(const __grid_constant__ UnfoldParams P) {
+  extern __shared__ float2 unf_smem[];
+  const int lane = threadIdx.x & 31;
+  const int U = P.U, B = P.B;
+  const int gst = U + 1;
+  float2* sq0 = unf_smem + (threadIdx.x >> 5) * proj_pair_warp_elems(U);
+  float2* sG0 = sq0 + 2 * 32;
+  const int hh = lane >> 4;
+  const int j = lane & 15;
+  const long long npairs = (P.samples + 1) / 2;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long pi = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pi < npairs;
+       pi += nw) {
+    // G = H^H H and q0 = H^H y of both samples, one after the other
+    for (int h = 0; h < 2; ++h) {
+      const long long s = 2 * pi + h;
+      if (s >= P.samples) break;
+      float2* sG = sG0 + h * U * gst;
+      gram_q0_tf32_global<UT>(P.H + (s / P.T) * B * U, P.Y + s * B, sq0 + 32 * h, sG, U, B, lane);
+      __syncwarp();
+      float2* ckG = P.ckpt + ckpt_g(P, s);
+      int rws, r0, u;
+      row_lane(U, lane, rws, r0, u);
+      if (r0 < rws)
+        for (int i = r0; i < U; i += rws) ckG[i * U + u] = sG[i * gst + u];
+    }
+    __syncwarp();
+    const long long s = 2 * pi + hh;
+    const bool valid = s < P.samples;
+    const bool act = valid && j < U;
+    const float2* sGh = sG0 + hh * U * gst;
+    float2 q = act ? sq0[32 * hh + j] : make_float2(0.0f, 0.0f);  // q0
+    const float nrm = act ? sGh[j * gst + j].x : 0.0f;
+    float2 z = make_float2(0.0f, 0.0f), zb = z, qs = z;
+    for (int k = 0; k < P.K; ++k) {
+      if (act) {
+        float2* ck = P.ckpt + ckpt_qz(P, k, s);
+        ck[j] = q;
+        ck[U + j] = z;
+      }
+      float d, p;
+      gains(nrm, __ldg(P.alpha + k), d, p);
+      qsweep16<false>(P, sGh, gst, j, q, z, d, p, __ldg(P.omega + k), zb, qs);
+    }
+    if (act) {
+      const long long o = s * U + j;
+      P.xhat[o] = z;
+      if (P.llr) {
+        float d, p;
+        gains(nrm, __ldg(P.alpha + P.K - 1), d, p);
+        DetectParams D = P.D;
+        D.rho_scale = P.es / __ldg(P.N0 + s / P.T);
+        user_llr(z, nrm, p, D, P.llr + o * P.D.Q);
+      }
+    }
+    __syncwarp();  // sG and sq are rewritten by the next pair
+  }
+}
+
+__global__ void __launch_bounds__(128)
+ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
+  extern __shared__ float2 unf_smem[];
+  const int lane = threadIdx.x & 31;
+  const int U = P.U;
+  const int gst = U + 1;
+  const int K = P.K;
+  const int hh = lane >> 4;
+  const int j = lane & 15;
+  float2* sG0 = unf_smem + (threadIdx.x >> 5) * 2 * U * gst;
+  const long long npairs = (P.samples + 1) / 2;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long pi = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pi < npairs;
+       pi += nw) {
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      const long long s2 = 2 * pi + h;
+      if (s2 >= P.samples) break;
+      const float2* ckG = P.ckpt + ckpt_g(P, s2);
+      float2* sG = sG0 + h * U * gst;
+      int rws, r0, u;
+      row_lane(U, lane, rws, r0, u);
+      if (r0 < rws)
+        for (int i = r0; i < U; i += rws) sG[i * gst + u] = ckG[i * U + u];
+    }
+    __syncwarp();
+    const long long s = 2 * pi + hh;
+    const bool valid = s < P.samples;
+    const bool act = valid && j < U;
+    const long long w = valid ? s / P.T : 0;
+    const float2* sG = sG0 + hh * U * gst;
+    const float nrm = act ? sG[j * gst + j].x : 0.0f;
+    // ---- adjoint of the soft output and of xhat (lane j)
+    float2 zbar = make_float2(0.0f, 0.0f);
+    float al_mu = 0.0f;
+    if (act) {
+      const long long o = s * U + j;
+      if (P.dxhat) zbar = __ldg(P.dxhat + o);
+      if (P.dllr) {
+        float d, p;
+        gains(nrm, __ldg(P.alpha + K - 1), d, p);
+        if (p > 0.0f) {
+          const float2 z = __ldg(P.xhat + o);
+          const float rho = nrm * P.es / __ldg(P.N0 + w);
+          const float inv = 1.0f / (p * P.D.sqrt_es);
+          const float* g = P.dllr + o * P.D.Q;
+          const float xr = z.x * inv;
+          const float sr = dimension_llr_slope(xr, rho, P.D, g);
+          zbar.x += sr * inv;
+          float mubar = -sr * xr / p;
+          if (!P.D.bpsk) {
+            const float xi = z.y * inv;
+            const float si = dimension_llr_slope(xi, rho, P.D, g + P.D.nb);
+            zbar.y += si * inv;
+            mubar -= si * xi / p;
+          }
+          al_mu = mubar * (-p * d);
+        }
+      }
+    }
+    al_mu = half_sum(al_mu);
+    float2 qbar = make_float2(0.0f, 0.0f);
+    float* part = P.partial + s * 2 * K;
+    for (int k = K - 1; k >= 0; --k) {
+      const float om = __ldg(P.omega + k);
+      float d, p;
+      gains(nrm, __ldg(P.alpha + k), d, p);
+      float2 q = make_float2(0.0f, 0.0f), z = q;
+      if (act) {
+        const float2* ck = P.ckpt + ckpt_qz(P, k, s);
+        q = ck[j];
+        z = ck[U + j];
+      }
+      float2 zb = make_float2(0.0f, 0.0f), qs = zb;
+      qsweep16<true>(P, sG, gst, j, q, z, d, p, om, zb, qs);
+      float om_l = 0.0f, al_l = 0.0f;  // lane u accumulates the terms of user u
+      // hs (lane l) = G[:, l]^H q', kept current as in the one-sample kernel
+      float2 hs = make_float2(0.0f, 0.0f);
+      for (int i = 0; i < U; ++i) {
+        const float2 qi = shfl2_16(qbar, i);
+        const float2 g = j < U ? sG[i * gst + j] : make_float2(0.0f, 0.0f);
+        hs.x = fmaf(g.x, qi.x, fmaf(g.y, qi.y, hs.x));
+        hs.y = fmaf(g.x, qi.y, fmaf(-g.y, qi.x, hs.y));
+      }
+      for (int u = U - 1; u >= 0; --u) {
+        const float2 hr = hs;  // lane u: G[:, u]^H q'
+        float2 dq = make_float2(0.0f, 0.0f);
+        if (j == u) {
+          const float wr0 = fmaf(d, qs.x, p * zb.x);
+          const float wi0 = fmaf(d, qs.y, p * zb.y);
+          float cr = wr0, ci = wi0;
+          project(cr, ci, P.D);
+          float mr = 1.0f, mi = 1.0f;
+          if (P.D.box) {
+            mr = fabsf(wr0) < P.D.box_a ? 1.0f : 0.0f;
+            mi = (!P.D.bpsk && fabsf(wi0) < P.D.box_a) ? 1.0f : 0.0f;
+          }
+          const float gr = zbar.x - hr.x, gi = zbar.y - hr.y;
+          om_l = fmaf(cr - zb.x, gr, fmaf(ci - zb.y, gi, om_l));
+          const float wbr = mr * om * gr, wbi = mi * om * gi;
+          zbar = make_float2(zbar.x - om * gr + p * wbr, zbar.y - om * gi + p * wbi);
+          dq = make_float2(d * wbr, d * wbi);
+          qbar = make_float2(qbar.x + dq.x, qbar.y + dq.y);
+          al_l -= d * d * fmaf(qs.x, wbr, qs.y * wbi) + p * d * fmaf(zb.x, wbr, zb.y * wbi);
+        }
+        dq = shfl2_16(dq, u);
+        const float2 g = j < U ? sG[u * gst + j] : make_float2(0.0f, 0.0f);
+        hs.x = fmaf(g.x, dq.x, fmaf(g.y, dq.y, hs.x));
+        hs.y = fmaf(g.x, dq.y, fmaf(-g.y, dq.x, hs.y));
+      }
+      float om_bar = half_sum(om_l);
+      float al_bar = half_sum(al_l);
+      if (k == K - 1) al_bar += al_mu;
+      if (valid && j == 0) {
+        part[2 * k] = om_bar;
+        part[2 * k + 1] = al_bar;
+      }
+    }
+  }
+}
+
 // cudaFuncSetAttribute once per (device, kernel, size): the launches below
 // stay free of attribute calls (and capturable) after the first one.
 cudaError_t allow_smem(const void* fn, size_t smem) {
@@ -742,18 +1010,41 @@ cudaError_t launch_proj_fwd(const UnfoldParams& P, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-template <int NA>
-cudaError_t launch_proj(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
-  if (!backward) {
-    if (P.U <= 8) return launch_proj_fwd<NA, 1>(P, stream);
-    if (P.U <= 16) return launch_proj_fwd<NA, 2>(P, stream);
-    return launch_proj_fwd<NA, 4>(P, stream);
-  }
-  const size_t smem = 4ull * P.U * (P.U + 1) * sizeof(float2);
-  const void* fn = reinterpret_cast<const void*>(ocd_unfolded_proj_backward_kernel);
+constexpr int kProjFwdPairWarps = 4;  // warps per CTA of the paired forward kernel
+
+template <int UT>
+cudaError_t launch_proj_fwd_pair(const UnfoldParams& P, cudaStream_t stream) {
+  const size_t smem = (size_t)kProjFwdPairWarps * proj_pair_warp_elems(P.U) * sizeof(float2);
+  const void* fn = reinterpret_cast<const void*>(ocd_unfolded_proj_forward_pair_kernel<UT>);
   cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  ocd_unfolded_proj_backward_kernel<<<grid, 128, smem, stream>>>(P);
+  const long long npairs = (P.samples + 1) / 2;
+  const unsigned grid = (unsigned)((npairs + kProjFwdPairWarps - 1) / kProjFwdPairWarps);
+  ocd_unfolded_proj_forward_pair_kernel<UT><<<grid, 32 * kProjFwdPairWarps, smem, stream>>>(P);
+  return cudaGetLastError();
+}
+
+// U <= 16: two samples per warp; larger U: one sample per warp.
+template <int NA>
+cudaError_t launch_proj(const UnfoldParams& P, bool backward, unsigned grid, cudaStream_t stream) {
+  const bool pair = P.U <= 16;
+  if (!backward) {
+    if (P.U <= 8) return launch_proj_fwd_pair<1>(P, stream);
+    if (P.U <= 16) return launch_proj_fwd_pair<2>(P, stream);
+    return launch_proj_fwd<NA, 4>(P, stream);
+  }
+  const size_t smem = (pair ? 8ull : 4ull) * P.U * (P.U + 1) * sizeof(float2);
+  const void* fn = pair ? reinterpret_cast<const void*>(ocd_unfolded_proj_backward_pair_kernel)
+                        : reinterpret_cast<const void*>(ocd_unfolded_proj_backward_kernel);
+  cudaError_t e = allow_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  if (pair) {
+    const long long need = ((P.samples + 1) / 2 + 3) / 4;  // 4 warps per CTA, a pair per warp
+    if ((long long)grid > need) grid = (unsigned)need;
+    ocd_unfolded_proj_backward_pair_kernel<<<grid, 128, smem, stream>>>(P);
+  } else {
+    ocd_unfolded_proj_backward_kernel<<<grid, 128, smem, stream>>>(P);
+  }
   return cudaGetLastError();
 }
 
