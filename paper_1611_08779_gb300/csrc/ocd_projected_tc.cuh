@@ -9,37 +9,40 @@
 //     Y-row t:   (Re y_{t,a}, Im y_{t,a})_a       (the received row as stored)
 // the dot product of Re-row u with Y-row t is Re(h_u^H y_t) and of Im-row u
 // with it Im(h_u^H y_t); with Re-row j in place of the Y-row they give
-// Re G_uj and Im G_uj.  So one shared-memory buffer per staged block holds
-// the rows [Y (YR) | Re (32) | Im (32)], and ONE MMA per K slice with
-//     A = rows YR .. YR + 63 (M = 64),  B = rows 0 .. YR + 31 (N = YR + 32)
-// accumulates q0 (columns 0 .. YR - 1) and G (columns YR .. YR + 31) at once.
+// Re G_uj and Im G_uj.  Two subcarriers a, b share every MMA: per K slice of
+// 8, A = [Re_a | Re_b | Im_a | Im_b] (M = 128, in tensor memory, row i in
+// TMEM lane i) and B = [Y_a | Y_b | Re_a | Re_b] (N = 2 YR + 64, in shared
+// memory) accumulate q0 (columns 0 .. 2 YR - 1) and G (the rest) of both;
+// the blocks that mix a with b are computed and dropped.
 // FP32-level accuracy: A B^T = Ah Bh^T + Ah Bl^T + Al Bh^T with hi = the value
 // as stored (the tensor core reads the leading 19 bits of an FP32 operand:
 // it truncates, measured) and lo = value - trunc(value); the dropped Al Bl^T
 // and the truncation of lo leave about 2^-20 relative error per product.
 //
-// One CTA (10 warps) per SM, persistent over subcarriers blockIdx.x +
-// i gridDim.x, blocks of 16 antennas (one 128-byte K atom per operand row):
-//   warp 0      producer: per block a bulk copy of the 16 channel rows and a
-//               2-D tensor copy of the YR received rows (128-byte swizzle, the
-//               operand layout itself) into a deep ring of raw stages, so
-//               that about 70 KB per SM are in flight;
-//   warps 2-5   transform: raw stage -> operand stage (a shallower ring):
-//               channel rows -> Re/Im rows (hi and lo), received rows copied
-//               with their lo rows;
-//   warp 1      one thread issues 3 MMAs per K slice of 8 into the
-//               subcarrier's TMEM slot and commits each block (the stage is
-//               free again) and each subcarrier (accumulators ready);
+// One CTA (14 warps, all 512 TMEM columns) per SM, persistent over
+// subcarriers blockIdx.x + i gridDim.x, blocks of 16 antennas (one 128-byte
+// K atom per operand row):
+//   warp 0      producer: per pair and block a bulk copy of the 16 channel
+//               rows and a 2-D tensor copy of the YR received rows (128-byte
+//               swizzle, the operand layout itself) of each subcarrier into
+//               a ring of raw stages;
+//   warps 2-5   transform, one per TMEM lane quarter: a thread (= user)
+//               writes its Re- or Im-row, hi and lo, into the A stage with
+//               tcgen05.st; the Re warps also store their rows into B, the
+//               Im warps copy the received rows with their lo rows;
+//   warp 1      one thread issues 3 MMAs per K slice (A from TMEM) into the
+//               pair's TMEM slot and commits each block (the stage is free
+//               again) and each pair (accumulators ready);
 //   warps 6-13  epilogue, two per TMEM lane quarter: groups of 8 subcarriers
-//               (4 pairs, every TMEM slot) are drained from TMEM (rows 32q ..
-//               32q + 31 of an M = 128 accumulator sit in lane quarter q),
-//               each slot released as soon as it is read; then each warp runs
-//               the preprocessing, the K sweeps and the outputs of one of them.
-// Eight TMEM slots of 64 columns (two groups of four) let the MMAs of one
-// group run under the epilogue of the previous one.  Every wait is bounded
-// in wall time; a wait that expires sets the fault word and a shared abort
-// flag that ends every role's loop, and the async copies and MMAs in flight
-// are waited for (bounded) before the TMEM is released.
+//               (4 pairs, every accumulator slot) are drained from TMEM, each
+//               slot released as soon as it is read; then each warp runs the
+//               preprocessing, the K sweeps and the outputs of one of them.
+// TMEM: two A stages of 64 columns (hi, lo), then four accumulator slots of
+// 96 columns, so the MMAs of one group run under the epilogue of the
+// previous one.  Every wait is bounded in wall time; a wait that expires
+// sets the fault word and a shared abort flag that ends every role's loop,
+// and the async copies and MMAs in flight are waited for (bounded) before
+// the TMEM is released.
 #pragma once
 
 #include "ocd_projected_wide.cuh"
@@ -48,25 +51,25 @@
 namespace ocd {
 
 #ifndef OCD_TC_RAW_STAGES
-#define OCD_TC_RAW_STAGES 3   // pair blocks whose copies may be in flight (36 KB per SM)
+#define OCD_TC_RAW_STAGES 4   // pair blocks whose copies may be in flight (48 KB per SM)
 #endif
 #ifndef OCD_TC_OP_STAGES
-#define OCD_TC_OP_STAGES 2    // operand buffers (transform ahead of the MMAs)
+#define OCD_TC_OP_STAGES 2    // operand stages (transform ahead of the MMAs)
 #endif
 
-// Two subcarriers a, b share every MMA ("pair"): the operand rows are
-//   [Y_a (YR) | Y_b (YR) | Re_a (32) | Re_b (32) | Im_a (32) | Im_b (32)]
-// with A = the last 128 rows (M = 128: TMEM lane i = row i) and B = the first
-// 2 YR + 64 rows (N = 2 YR + 64); the accumulator blocks that mix a with b
-// are computed and dropped.
+// Two subcarriers a, b share every MMA ("pair").  A = the 128 rows
+// [Re_a | Re_b | Im_a | Im_b] (M = 128, TMEM lane i = row i) lives in tensor
+// memory; B = the 2 YR + 64 rows [Y_a | Y_b | Re_a | Re_b] (N = 2 YR + 64) in
+// shared memory.  The accumulator blocks that mix a with b are computed and
+// dropped.
 template <int YR>
 struct TcShape {
   static_assert(YR == 8 || YR == 16, "received rows per subcarrier: 8 or 16");
   static constexpr int kBA = 16;                          // antennas per staged block
   static constexpr int kN = 2 * YR + 64;                  // MMA N
-  static constexpr int kRowA = 2 * YR;                    // first A row
-  static constexpr int kRows = 2 * YR + 128;              // operand rows
-  static constexpr int kOpBytes = kRows * 128;            // one operand buffer (hi or lo)
+  static constexpr int kRowRe = 2 * YR;                   // first Re row of B
+  static constexpr int kRows = 2 * YR + 64;               // B rows
+  static constexpr int kOpBytes = kRows * 128;            // one B buffer (hi or lo)
   static constexpr int kOpStageBytes = 2 * kOpBytes;      // hi and lo
   static constexpr int kOpStages = OCD_TC_OP_STAGES;
   // raw stage: Y_a, Y_b boxes (swizzled, each YR rows), then H_a, H_b
@@ -74,9 +77,13 @@ struct TcShape {
   static constexpr int kRawH = kBA * 32 * 8;              // one subcarrier's channel rows
   static constexpr int kRawStageBytes = 2 * kRawY + 2 * kRawH;
   static constexpr int kRawStages = OCD_TC_RAW_STAGES;
-  static constexpr int kSlots = 4;                        // TMEM accumulator slots (pairs)
-  static constexpr int kSlotCols = 128;
-  static constexpr int kTmemCols = kSlots * kSlotCols;    // 512: the whole TMEM of an SM
+  // tensor memory: A stages (hi in columns 0-31, lo in 32-63 of a stage),
+  // then the accumulator slots
+  static constexpr int kACols = 64;
+  static constexpr int kSlots = 4;                        // accumulator slots (pairs)
+  static constexpr int kSlotCols = 96;
+  static constexpr int kAccCol = kOpStages * kACols;
+  static constexpr int kTmemCols = 512;                   // the whole TMEM of an SM
   static constexpr int kEpiG = 32 * WideShape::kGRow * 4;  // G rows (re run | im run | pad)
   static constexpr int kEpiQ = 16 * 32 * 8;               // q0, then z, [symbol][user]
   static constexpr int kEpiPre = 32 * 16;                 // (d^-1, p, rho~ step^2, u scale)
@@ -89,9 +96,10 @@ struct TcShape {
   static constexpr int kOffTmem = kOffBar + 8 * kNumBars;
   static constexpr int kOffAbort = kOffTmem + 4;
   static constexpr int kBytes = kOffAbort + 4;
-  static constexpr int kTransformWarps = 4;
+  static constexpr int kTransformWarps = 4;               // one per TMEM lane quarter of A
   static constexpr int kThreads = 32 * (2 + kTransformWarps + kEpiWarps);  // 448
   static_assert(kEpiWarps == 2 * kSlots, "a group of subcarriers fills the TMEM slots");
+  static_assert(kAccCol + kSlots * kSlotCols <= kTmemCols, "A stages and accumulators fit TMEM");
   static_assert(kOpBytes % 1024 == 0 && kRawY % 1024 == 0 && kRawStageBytes % 1024 == 0,
                 "1024-byte swizzle phase");
   static_assert(kN <= kSlotCols && kN % 16 == 0, "one pair's accumulators fit a slot");
@@ -281,7 +289,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
         }
         TC_ADD(0, c0);
         tc_fence_after();
-        const uint32_t d = tbase + (uint32_t)(slot * S::kSlotCols);
+        const uint32_t d = tbase + (uint32_t)(S::kAccCol + slot * S::kSlotCols);
         for (int blk = 0; blk < nblk; ++blk, ++g) {
           const int st = (int)(g % O);
           TC_CLOCK(c1);
@@ -292,21 +300,22 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
           TC_ADD(1, c1);
           TC_CLOCK(c2);
           tc_fence_after();
-          // descriptors of the stage; the K slices are 32 bytes (2 units of
-          // the start-address field) apart
+          // A: TMEM columns of the stage (hi, then lo 32 columns on), 8 per
+          // K slice; B: descriptors of the stage, K slices 32 bytes (2 units
+          // of the start-address field) apart
+          const uint32_t ah = tbase + (uint32_t)(st * S::kACols);
+          const uint32_t al = ah + 32u;
           const uint32_t hi = sbase + st * S::kOpStageBytes;
-          const uint64_t ah = sw128_desc(hi + S::kRowA * 128);
-          const uint64_t al = sw128_desc(hi + S::kOpBytes + S::kRowA * 128);
           const uint64_t bh = sw128_desc(hi);
           const uint64_t bl = sw128_desc(hi + S::kOpBytes);
-          tc_mma_tf32(d, ah, bh, idesc, blk > 0 ? 1u : 0u);
-          tc_mma_tf32(d, ah, bl, idesc, 1u);
-          tc_mma_tf32(d, al, bh, idesc, 1u);
+          tc_mma_tf32_ts(d, ah, bh, idesc, blk > 0 ? 1u : 0u);
+          tc_mma_tf32_ts(d, ah, bl, idesc, 1u);
+          tc_mma_tf32_ts(d, al, bh, idesc, 1u);
 #pragma unroll
           for (int ks = 1; ks < 4; ++ks) {
-            tc_mma_tf32(d, ah + 2 * ks, bh + 2 * ks, idesc, 1u);
-            tc_mma_tf32(d, ah + 2 * ks, bl + 2 * ks, idesc, 1u);
-            tc_mma_tf32(d, al + 2 * ks, bh + 2 * ks, idesc, 1u);
+            tc_mma_tf32_ts(d, ah + 8 * ks, bh + 2 * ks, idesc, 1u);
+            tc_mma_tf32_ts(d, ah + 8 * ks, bl + 2 * ks, idesc, 1u);
+            tc_mma_tf32_ts(d, al + 8 * ks, bh + 2 * ks, idesc, 1u);
           }
           tc_commit(bar_empty(st));
           TC_ADD(2, c2);
@@ -321,7 +330,16 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
     __syncwarp();
   } else if (warp < EW0) {
     // ---------------- transform -------------------------------------------
-    const int tt = tid - 64;  // 0 .. 32 NTW - 1
+    // Warp with TMEM lane quarter q writes A rows 32q + u (u = lane): the
+    // Re-row (q < 2) or the Im-row (q >= 2) of user u of half h = q & 1,
+    // hi and lo, with tcgen05.st.  The Re warps also store their rows into
+    // B (the G columns), the Im warps copy the received rows of their half.
+    // An absent half b transforms stale data into rows nobody reads.
+    const int q = warp & 3;
+    const int h = q & 1;
+    const bool imrow = q >= 2;
+    const int u = lane;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     long long g = 0;
     bool ok = true;
     for (long long p = 0; p < npairs && ok; ++p) {
@@ -342,44 +360,60 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
         }
         TC_ADD(1, c1);
         TC_CLOCK(c2);
+        tc_fence_after();
         const int bb = min(S::kBA, B - blk * S::kBA);
         unsigned char* hi = base + os * S::kOpStageBytes;
         unsigned char* lo = hi + S::kOpBytes;
         const unsigned char* rawst = base + S::kOffRaw + rs * S::kRawStageBytes;
-        // channel: item = (half h, user u, antenna pair ap) -> one 16-byte
-        // chunk of K (antennas 2ap, 2ap + 1) in the Re-row and the Im-row of
-        // u (an absent half b transforms stale data into rows nobody reads)
+        const float2* raw = reinterpret_cast<const float2*>(rawst + 2 * S::kRawY + h * S::kRawH);
+        const uint32_t ta = tbase + lane_base + (uint32_t)(os * S::kACols);
+        const int row = S::kRowRe + 32 * h + u;  // this user's B row (Re warps)
+        const bool uok = u < U;
+        // K chunk c = antennas 4c .. 4c + 3 (8 columns, two 16-byte chunks)
 #pragma unroll
-        for (int j = 0; j < 512 / (32 * NTW); ++j) {
-          const int item = tt + 32 * NTW * j;
-          const int h = item >> 8;
-          const int u = item & 31;
-          const int ap = (item >> 5) & 7;
-          const int a0 = 2 * ap;
-          const float2* raw = reinterpret_cast<const float2*>(rawst + 2 * S::kRawY + h * S::kRawH);
-          const bool uok = u < U;
-          const float2 z2 = make_float2(0.0f, 0.0f);
-          const float2 h0 = (uok && a0 < bb) ? raw[a0 * U + u] : z2;
-          const float2 h1 = (uok && a0 + 1 < bb) ? raw[(a0 + 1) * U + u] : z2;
-          const float4 rh = make_float4(h0.x, h0.y, h1.x, h1.y);
-          const float4 ih = make_float4(-h0.y, h0.x, -h1.y, h1.x);
-          const int rr = S::kRowA + 32 * h + u;
-          const int ri = S::kRowA + 64 + 32 * h + u;
-          const int orr = rr * 128 + ((ap ^ (rr & 7)) << 4);
-          const int ori = ri * 128 + ((ap ^ (ri & 7)) << 4);
-          *reinterpret_cast<float4*>(hi + orr) = rh;
-          *reinterpret_cast<float4*>(lo + orr) = tf32_lo4(rh);
-          *reinterpret_cast<float4*>(hi + ori) = ih;
-          *reinterpret_cast<float4*>(lo + ori) = tf32_lo4(ih);
+        for (int c = 0; c < 4; ++c) {
+          float v[8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int a = 4 * c + k;
+            const float2 x = (uok && a < bb) ? raw[a * U + u] : make_float2(0.0f, 0.0f);
+            v[2 * k] = imrow ? -x.y : x.x;
+            v[2 * k + 1] = imrow ? x.x : x.y;
+          }
+          float w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            w[k] = v[k] - __uint_as_float(__float_as_uint(v[k]) & 0xffffe000u);
+          tmem_st8(ta + 8 * c, __float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]),
+                   __float_as_uint(v[3]), __float_as_uint(v[4]), __float_as_uint(v[5]),
+                   __float_as_uint(v[6]), __float_as_uint(v[7]));
+          tmem_st8(ta + 32 + 8 * c, __float_as_uint(w[0]), __float_as_uint(w[1]),
+                   __float_as_uint(w[2]), __float_as_uint(w[3]), __float_as_uint(w[4]),
+                   __float_as_uint(w[5]), __float_as_uint(w[6]), __float_as_uint(w[7]));
+          if (!imrow) {
+            const int o0 = row * 128 + (((2 * c) ^ (row & 7)) << 4);
+            const int o1 = row * 128 + (((2 * c + 1) ^ (row & 7)) << 4);
+            *reinterpret_cast<float4*>(hi + o0) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(hi + o1) = make_float4(v[4], v[5], v[6], v[7]);
+            *reinterpret_cast<float4*>(lo + o0) = make_float4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<float4*>(lo + o1) = make_float4(w[4], w[5], w[6], w[7]);
+          }
         }
-        // received rows of both halves, as staged (the same swizzled layout)
-        // and their lo parts
-        for (int c = tt; c < 2 * YR * 8; c += 32 * NTW) {
-          const float4 v = *reinterpret_cast<const float4*>(rawst + 16 * c);
-          *reinterpret_cast<float4*>(hi + 16 * c) = v;
-          *reinterpret_cast<float4*>(lo + 16 * c) = tf32_lo4(v);
+        if (imrow) {
+          // received rows of half h, as staged (the same swizzled layout, the
+          // same 1024-byte phase) and their lo parts
+          const unsigned char* ys = rawst + h * S::kRawY;
+          const int yo = h * S::kRawY;
+#pragma unroll
+          for (int c = lane; c < YR * 8; c += 32) {
+            const float4 x = *reinterpret_cast<const float4*>(ys + 16 * c);
+            *reinterpret_cast<float4*>(hi + yo + 16 * c) = x;
+            *reinterpret_cast<float4*>(lo + yo + 16 * c) = tf32_lo4(x);
+          }
         }
+        tmem_wait_st();
         fence_proxy_async();
+        tc_fence_before();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(bar_free(rs));
@@ -416,7 +450,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
         TC_ADD(0, c1);
         tc_fence_after();
         uint32_t vq[16], vg0[16], vg1[16];
-        const uint32_t ta = tbase + lane_base + (uint32_t)(slot * S::kSlotCols);
+        const uint32_t ta = tbase + lane_base + (uint32_t)(S::kAccCol + slot * S::kSlotCols);
         tmem_ld16(ta + cq, vq);
         tmem_ld16(ta + cg, vg0);
         tmem_ld16(ta + cg + 16, vg1);
