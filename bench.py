@@ -800,10 +800,12 @@ def measure_batched(args):
     arms["per_cell_launches"] = timed(per_cell, steps)
     arms["batched_default_tiles"] = timed(lambda: ocd.ocd_detect_batched(cells, workspace=ws), steps)
     t0 = time.perf_counter()
-    tune = ocd.ocd_autotune_batched(cells, reps=2, workspace=ws)
+    tune = ocd.ocd_autotune_batched(cells, reps=3, workspace=ws)
     tune_s = time.perf_counter() - t0
     algo_of = {(e["B"], e["U"], e["T"]): e["algo"] for e in tune.entries}
-    bound = [batched_bound_s(s, hbm, fma_tf, algo_of[(s["B"], s["U"], s["T"])] == 2) for s in specs]
+    projected = (2, 3, 4)  # OCD_ALGO_PROJECTED, _PROJECTED_WARP, _PROJECTED_TC
+    bound = [batched_bound_s(s, hbm, fma_tf, algo_of[(s["B"], s["U"], s["T"])] in projected)
+             for s in specs]
     t_bound = sum(b for b, _ in bound)
     nbytes = sum(n for _, n in bound)
     arms["batched_tuned"] = timed(lambda: ocd.ocd_detect_batched(cells, tune=tune, workspace=ws), steps)

@@ -221,7 +221,10 @@ typedef struct {
  * ocd_autotune_batched.  Zero fields take the defaults. */
 typedef struct {
   int B, U, T, storage;  /* key */
-  int algo;              /* OCD_ALGO_RESIDUAL or OCD_ALGO_PROJECTED */
+  int algo;              /* OCD_ALGO_RESIDUAL, OCD_ALGO_PROJECTED (its default kernel),
+                            OCD_ALGO_PROJECTED_WARP or OCD_ALGO_PROJECTED_TC (a cell the
+                            tcgen05 kernel does not fit takes the default kernel; a cell
+                            the projected form does not fit takes the residual form) */
   int symbols_per_item;  /* residual form: symbols per work item, 1 or 2 */
   int lanes_per_item;    /* residual form: lanes per work item, power of two <= 32 */
   int sc_per_ticket;     /* projected form: subcarriers per ticket, 1..256 (0 when
@@ -279,13 +282,21 @@ int ocd_detect_batched_static(const ocd_cell_t* cells, int ncells, const ocd_tun
                               cudaStream_t stream);
 
 /*
- * ocd_autotune_batched -- for every distinct (B, U, T, storage) among the
- * cells, times the candidate tiles (each arrangement the shape supports;
- * symbols and lanes per item for the residual form, subcarriers per ticket
- * for the projected form) on those cells' own buffers, `reps` timed runs
- * (1..100) after one warm-up, and writes the fastest choice per shape to
- * `tune` (replacing its contents).  Overwrites the cells' outputs;
- * synchronizes `stream`.  At most OCD_TUNE_MAX_ENTRIES shapes.
+ * ocd_autotune_batched -- builds a tune table for exactly this batch, on the
+ * cells' own buffers, with `reps` timed runs (1..100) after one warm-up per
+ * measurement.  Phase 1: for every distinct (B, U, T, storage), the
+ * candidate tiles (each arrangement the shape supports; symbols and lanes per
+ * item for the residual form, subcarriers per ticket for the projected form)
+ * timed on that shape's cells alone; the fastest is kept.  Phase 2: the
+ * whole batch timed at once (what the shapes' launches do to each other on
+ * the internal streams), first with the defaults written out as a table,
+ * then with one shape at a time changed to its other choices (the warp-level
+ * or the tcgen05 kernel for 17-32 users, subcarriers per ticket halved or
+ * doubled, the other arrangement); a change is kept only when the batch
+ * gets more than 1.5% faster.  time_us of an entry is its shape's time
+ * alone.  Writes the result to `tune` (replacing its contents).  Overwrites
+ * the cells' outputs; synchronizes `stream`.  At most OCD_TUNE_MAX_ENTRIES
+ * shapes.
  */
 int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
                          size_t workspace_bytes, int reps, ocd_tune_t* tune,

@@ -168,8 +168,11 @@ def ocd_detect_batched_static(cells, tune: Tune | None = None,
 
 def ocd_autotune_batched(cells, reps: int = 3, workspace: torch.Tensor | None = None,
                          stream: torch.cuda.Stream | None = None) -> Tune:
-    """Times the candidate tiles per cell shape on the cells' own buffers
-    (their outputs are overwritten) and returns the fastest choices."""
+    """Tune table for this batch, timed on the cells' own buffers (their
+    outputs are overwritten): the fastest tile per cell shape on that shape's
+    cells alone, then refined on the whole batch (defaults, the 32-user
+    kernel choice, tickets, arrangement per shape; a change kept only when
+    the batch gets faster)."""
     lib = _native.load()
     arr, dev = _cell_array(cells)
     tune = Tune()

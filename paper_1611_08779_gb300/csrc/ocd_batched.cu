@@ -78,17 +78,27 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
   const bool wide = can_wide(cp.P);
   const bool tma_ok = can_tma32(cp.P) || wide;
   int algo = c.algo;
-  if (algo == OCD_ALGO_PROJECTED_TC && !can_tc(cp.P))
-    return fail(OCD_ERR_UNSUPPORTED, "the tcgen05 kernel needs 16 < U <= 32, T <= %d, float32 "
-                "storage, even B and 16-byte aligned H and Y", ocd::kTcMaxSymbols);
+  // a cell with OCD_ALGO_AUTO takes its shape's tune entry; a tune entry's
+  // tcgen05 choice falls back to the default kernel for a cell it does not
+  // fit (alignment differs between cells of one shape)
+  bool from_tune = false;
+  if (algo == OCD_ALGO_AUTO && te && te->algo >= OCD_ALGO_RESIDUAL && te->algo <= OCD_ALGO_PROJECTED_TC) {
+    algo = te->algo;
+    from_tune = true;
+  }
+  if (algo == OCD_ALGO_PROJECTED_TC && !can_tc(cp.P)) {
+    if (!from_tune)
+      return fail(OCD_ERR_UNSUPPORTED, "the tcgen05 kernel needs 16 < U <= 32, T <= %d, float32 "
+                  "storage, even B and 16-byte aligned H and Y", ocd::kTcMaxSymbols);
+    algo = OCD_ALGO_PROJECTED;
+  }
   const bool warp_only = algo == OCD_ALGO_PROJECTED_WARP;
   const bool use_tc = algo == OCD_ALGO_PROJECTED_TC;
   if (warp_only || use_tc) algo = OCD_ALGO_PROJECTED;
-  if (algo == OCD_ALGO_AUTO && te && (te->algo == OCD_ALGO_RESIDUAL || te->algo == OCD_ALGO_PROJECTED))
-    algo = te->algo;
   // default without a tune entry: the bulk-copy projected form wherever it
   // applies, one symbol included (as the single-problem path at T = 1)
   if (algo == OCD_ALGO_AUTO) algo = tma_ok ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+  if (algo == OCD_ALGO_PROJECTED && !tma_ok && from_tune) algo = OCD_ALGO_RESIDUAL;
   if (algo == OCD_ALGO_PROJECTED && !tma_ok)
     return fail(OCD_ERR_UNSUPPORTED, "batched projected form needs float32 storage, even B "
                 "and 16-byte aligned H and Y (U=%d B=%d)", c.U, c.B);
@@ -488,19 +498,47 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(e, "cudaEventCreate");
   }
-  std::vector<ocd_cell_t> group;
+  // Mean time (us) of `reps` enqueues of `n` cells after one warm-up, with
+  // the tune table `t` or the single entry `force`.
+  auto time_run = [&](const ocd_cell_t* cs, int n, const ocd_tune_t* t,
+                      const ocd_tune_entry_t* force, float& us) -> int {
+    int s2 = run_batch(cs, n, t, force, workspace, stream);  // warm-up
+    if (s2 != OCD_OK) return s2;
+    cudaError_t ee = cudaEventRecord(e0, stream);
+    for (int r = 0; r < reps && s2 == OCD_OK && ee == cudaSuccess; ++r)
+      s2 = run_batch(cs, n, t, force, workspace, stream);
+    if (ee == cudaSuccess) ee = cudaEventRecord(e1, stream);
+    if (ee == cudaSuccess) ee = cudaEventSynchronize(e1);
+    if (s2 != OCD_OK) return s2;
+    if (ee != cudaSuccess) return cuda_fail(ee, "autotune timing");
+    float ms = 0.0f;
+    ee = cudaEventElapsedTime(&ms, e0, e1);
+    if (ee != cudaSuccess) return cuda_fail(ee, "cudaEventElapsedTime");
+    us = 1000.0f * ms / reps;
+    return OCD_OK;
+  };
+
+  // Phase 1: per shape, the fastest tile on that shape's cells alone.
+  struct Shape {
+    std::vector<ocd_cell_t> group;  // the shape's cells (algo AUTO)
+    bool tma_all = false;           // every cell takes the projected form
+    bool lane_all = false;          // every cell runs the one-lane kernel
+    bool tc_all = false;            // every cell fits the tcgen05 kernel
+    bool wide = false;              // 17-32 users
+  };
+  std::vector<Shape> shapes;
   std::vector<bool> done(ncells, false);
   for (int i = 0; i < ncells && st == OCD_OK; ++i) {
     const ocd_cell_t& c = cells[i];
     if (done[i] || (long long)c.Nsc * c.T == 0) continue;
-    group.clear();
+    Shape sh;
     for (int j = i; j < ncells; ++j) {
       const ocd_cell_t& d = cells[j];
       if (!done[j] && d.B == c.B && d.U == c.U && d.T == c.T && d.storage == c.storage &&
           (long long)d.Nsc * d.T > 0) {
         ocd_cell_t g = d;
         g.algo = OCD_ALGO_AUTO;  // the candidate decides
-        group.push_back(g);
+        sh.group.push_back(g);
         done[j] = true;
       }
     }
@@ -510,31 +548,24 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
     }
     // candidates: projected (if the shape takes it) x tickets; residual x S x L
     std::vector<ocd_tune_entry_t> cand;
-    ocd::DetectParams P;
     Alphabet al;
     alphabet_of(c.qam_order, al);
-    build_params(c.H, c.Y, c.storage, c.Nsc, c.B, c.U, c.T, c.N0, c.Es, c.K, c.mode, al, c.xhat,
-                 c.llr, P);
     const ocd_tune_entry_t base = {c.B, c.U, c.T, c.storage, 0, 0, 0, 0, 0.0f};
-    bool tma_all = can_tma32(P) || can_wide(P);
-    for (const ocd_cell_t& g : group) {
+    sh.tma_all = sh.lane_all = sh.tc_all = true;
+    sh.wide = c.U > 16;
+    for (const ocd_cell_t& g : sh.group) {
       ocd::DetectParams Pg;
       build_params(g.H, g.Y, g.storage, g.Nsc, g.B, g.U, g.T, g.N0, g.Es, g.K, g.mode, al,
                    g.xhat, g.llr, Pg);
-      tma_all = tma_all && (can_tma32(Pg) || can_wide(Pg));
+      sh.tma_all = sh.tma_all && (can_tma32(Pg) || can_wide(Pg));
+      sh.lane_all = sh.lane_all && can_lane(Pg);
+      sh.tc_all = sh.tc_all && can_tc(Pg);
     }
-    bool lane_all = true;
-    for (const ocd_cell_t& g : group) {
-      ocd::DetectParams Pg;
-      build_params(g.H, g.Y, g.storage, g.Nsc, g.B, g.U, g.T, g.N0, g.Es, g.K, g.mode, al,
-                   g.xhat, g.llr, Pg);
-      lane_all = lane_all && can_lane(Pg);
-    }
-    if (lane_all) {  // the one-lane kernel has no tile to choose
+    if (sh.lane_all) {  // the one-lane kernel has no tile to choose
       ocd_tune_entry_t t = base;
       t.algo = OCD_ALGO_PROJECTED;
       cand.push_back(t);
-    } else if (tma_all && c.T >= 1) {
+    } else if (sh.tma_all && c.T >= 1) {
       for (int spt : {1, 2, 4, 8, 16, 32}) {
         ocd_tune_entry_t t = base;
         t.algo = OCD_ALGO_PROJECTED;
@@ -556,21 +587,10 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
     float best = INFINITY;
     ocd_tune_entry_t pick = base;
     for (const ocd_tune_entry_t& t : cand) {
-      const int ng = (int)group.size();
-      int s2 = run_batch(group.data(), ng, nullptr, &t, workspace, stream);  // warm-up
+      float us = 0.0f;
+      const int s2 = time_run(sh.group.data(), (int)sh.group.size(), nullptr, &t, us);
       if (s2 == OCD_ERR_UNSUPPORTED) continue;  // e.g. the tile does not fit
       if (s2 != OCD_OK) { st = s2; break; }
-      e = cudaEventRecord(e0, stream);
-      for (int r = 0; r < reps && s2 == OCD_OK && e == cudaSuccess; ++r)
-        s2 = run_batch(group.data(), ng, nullptr, &t, workspace, stream);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (s2 != OCD_OK) { st = s2; break; }
-      if (e != cudaSuccess) { st = cuda_fail(e, "autotune timing"); break; }
-      float ms = 0.0f;
-      e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) { st = cuda_fail(e, "cudaEventElapsedTime"); break; }
-      const float us = 1000.0f * ms / reps;
       if (us < best) {
         best = us;
         pick = t;
@@ -579,7 +599,89 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
     }
     if (st == OCD_OK) {
       if (!(best < INFINITY)) st = fail(OCD_ERR_UNSUPPORTED, "no tile fits shape B=%d U=%d T=%d", c.B, c.U, c.T);
-      else out.entry[out.n++] = pick;
+      else {
+        out.entry[out.n++] = pick;
+        shapes.push_back(std::move(sh));
+      }
+    }
+  }
+
+  // Phase 2: the whole batch.  Shapes timed alone do not show how their
+  // launches share the GPU on the internal streams (a tcgen05 launch holds
+  // every SM it runs on; persistent launches of other kernels fill SMs as
+  // they free up), so the table is refined on all cells at once: the
+  // defaults as a whole, then one shape at a time its other choices
+  // (kernel of a 32-user shape, tickets halved or doubled, the other
+  // arrangement), each kept only when the whole batch gets faster by more
+  // than the noise margin.
+  if (st == OCD_OK && out.n > 0) {
+    constexpr float kKeep = 0.985f;  // a change must save more than 1.5%
+    float best = 0.0f;
+    st = time_run(cells, ncells, &out, nullptr, best);
+    // the defaults, written out as explicit entries (tiles left at zero)
+    ocd_tune_t def = out;
+    for (int i = 0; i < def.n; ++i) {
+      ocd_tune_entry_t& t = def.entry[i];
+      t.algo = shapes[i].tma_all ? OCD_ALGO_PROJECTED : OCD_ALGO_RESIDUAL;
+      t.symbols_per_item = t.lanes_per_item = t.sc_per_ticket = 0;
+      t.time_us = 0.0f;
+    }
+    float us = 0.0f;
+    if (st == OCD_OK) st = time_run(cells, ncells, &def, nullptr, us);
+    if (st == OCD_OK && us < kKeep * best) {
+      out = def;
+      best = us;
+    }
+    for (int i = 0; i < out.n && st == OCD_OK; ++i) {
+      const Shape& sh = shapes[i];
+      if (sh.lane_all) continue;
+      std::vector<ocd_tune_entry_t> alt;
+      const ocd_tune_entry_t cur = out.entry[i];
+      const bool proj = cur.algo == OCD_ALGO_PROJECTED || cur.algo == OCD_ALGO_PROJECTED_WARP ||
+                        cur.algo == OCD_ALGO_PROJECTED_TC;
+      if (proj) {
+        if (sh.wide && sh.tc_all) {
+          for (int a : {OCD_ALGO_PROJECTED_WARP, OCD_ALGO_PROJECTED_TC}) {
+            ocd_tune_entry_t t = cur;
+            t.algo = a;
+            if (a != cur.algo) alt.push_back(t);
+          }
+        }
+        const int spt = cur.sc_per_ticket;
+        for (int f : {2, -2}) {
+          ocd_tune_entry_t t = cur;
+          t.sc_per_ticket = spt == 0 ? (f > 0 ? 16 : 1) : (f > 0 ? spt * 2 : spt / 2);
+          if (t.sc_per_ticket >= 1 && t.sc_per_ticket <= 256 && t.sc_per_ticket != spt) alt.push_back(t);
+        }
+        ocd_tune_entry_t r = cur;
+        r.algo = OCD_ALGO_RESIDUAL;
+        r.symbols_per_item = r.lanes_per_item = r.sc_per_ticket = 0;
+        alt.push_back(r);
+      } else if (sh.tma_all) {
+        ocd_tune_entry_t t = cur;
+        t.algo = OCD_ALGO_PROJECTED;
+        t.symbols_per_item = t.lanes_per_item = t.sc_per_ticket = 0;
+        alt.push_back(t);
+      }
+      for (const ocd_tune_entry_t& t : alt) {
+        ocd_tune_t trial = out;
+        trial.entry[i] = t;
+        trial.entry[i].time_us = 0.0f;
+        const int s2 = time_run(cells, ncells, &trial, nullptr, us);
+        if (s2 == OCD_ERR_UNSUPPORTED) continue;
+        if (s2 != OCD_OK) { st = s2; break; }
+        if (us < kKeep * best) {
+          out = trial;
+          best = us;
+        }
+      }
+    }
+    // entries changed in phase 2 carry the time of their shape alone
+    for (int i = 0; i < out.n && st == OCD_OK; ++i) {
+      if (out.entry[i].time_us > 0.0f) continue;
+      ocd_tune_entry_t t = out.entry[i];
+      st = time_run(shapes[i].group.data(), (int)shapes[i].group.size(), nullptr, &t, us);
+      if (st == OCD_OK) out.entry[i].time_us = us;
     }
   }
   cudaEventDestroy(e0);

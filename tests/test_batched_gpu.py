@@ -95,13 +95,18 @@ def test_autotuned_tiles_keep_parity():
     got = {(e["B"], e["U"], e["T"]) for e in tune.entries}
     assert got == shapes
     for e in tune.entries:
-        assert e["algo"] in (1, 2) and e["time_us"] > 0
-        if e["algo"] == 2:
-            # one symbol with U <= 8 runs the one-lane kernel: no ticket size
+        assert e["algo"] in (1, 2, 3, 4) and e["time_us"] > 0
+        if e["algo"] in (3, 4):
+            # the warp-level or the tcgen05 kernel: 17-32 users only
+            assert 16 < e["U"] <= 32
+        if e["algo"] in (2, 3, 4):
+            # one symbol with U <= 8 runs the one-lane kernel: no ticket size;
+            # 0 elsewhere is the default ticket size (kept by the whole-batch phase)
             lane = e["T"] == 1 and e["U"] <= 8
-            assert e["U"] <= 32 and (e["sc_per_ticket"] == 0 if lane else e["sc_per_ticket"] >= 1)
+            assert e["U"] <= 32 and (e["sc_per_ticket"] == 0 if lane else e["sc_per_ticket"] >= 0)
         else:
-            assert e["symbols_per_item"] in (1, 2) and e["lanes_per_item"] >= 1
+            # 0: the default tile (kept by the whole-batch phase)
+            assert e["symbols_per_item"] in (0, 1, 2) and e["lanes_per_item"] >= 0
     for c in cells:
         c.xhat.zero_()
         c.llr.zero_()
@@ -110,6 +115,29 @@ def test_autotuned_tiles_keep_parity():
     g = ocd.BatchedGraph(cells, tune=tune)
     g.launch()
     check_cells(specs, data, cells, "tuned graph")
+
+
+@pytest.mark.parametrize("T", [14, 20])
+def test_tune_entry_chooses_the_32_user_kernel(T):
+    # a tune entry may name the warp-level or the tcgen05 kernel; results are
+    # those of ocd_detect with the same kernel, and a cell the tcgen05 kernel
+    # does not fit (T > 16) takes the default kernel instead
+    specs = [{"B": 64, "U": 24, "T": T, "Nsc": 37, "K": 3, "mode": "box", "order": 16,
+              "snr_db": 14.0, "seed": 4100},
+             {"B": 64, "U": 24, "T": T, "Nsc": 21, "K": 3, "mode": "box", "order": 16,
+              "snr_db": 14.0, "seed": 4101}]
+    data, cells = build_cells(specs)
+    for algo, name in ((3, "projected_warp"), (4, "projected_tc")):
+        tune = ocd.Tune([{"B": 64, "U": 24, "T": T, "storage": 0, "algo": algo}])
+        for c in cells:
+            c.xhat.zero_()
+            c.llr.zero_()
+        ocd.ocd_detect_batched(cells, tune=tune)
+        torch.cuda.synchronize()
+        single = name if (name == "projected_warp" or T <= 16) else "projected"
+        for c in cells:
+            x, L = ocd.ocd_detect(c.H, c.Y, c.N0, c.Es, c.K, c.mode, c.qam_order, algo=single)
+            assert torch.equal(x, c.xhat) and torch.equal(L, c.llr), (T, name)
 
 
 def test_more_cells_than_one_launch_holds():
