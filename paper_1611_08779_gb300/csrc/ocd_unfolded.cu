@@ -456,11 +456,14 @@ __device__ __forceinline__ void qsweep(const UnfoldParams& P, const float2* sG, 
 }
 
 // G = H^H H (Hermitian, diagonal real) into sG (row stride U + 1) and
-// q0 = H^H y into sy[0 .. U) (over y), from the user-major channel copy sH,
-// as realified m16n8k8 TF32 MMAs with the two-part split (hi*hi, hi*lo +
+// q0 = H^H y into sy[0 .. U) (over y), from the user-major channel copy sH.
+// G: realified m16n8k8 TF32 MMAs with the two-part split (hi*hi, hi*lo +
 // lo*hi; FP32-level accuracy).  A k-step covers antennas 4s + t (lane t of a
 // quad): A = [Re H^H; Im H^H] of user tile m, B = the same entries of user
-// tile n (G) or the received vector in column 0 (q0).  UT = user tiles.
+// tile n.  q0 (one received vector: an MMA would use one column of eight)
+// by FP32 fmas on the same channel entries: lane (gq, t) sums
+// conj(h_{a,u}) y_a over its antennas a = t mod 4 in order, then the four
+// lanes of a quad add up as a tree.  UT = user tiles.
 // G = H^H H and q0 = H^H y (see gram_q0_tf32) from loaders hld(u, a) (user u,
 // antenna a; zero for u >= U is handled here, for a >= B by the loader) and
 // yld(a); q0 of user u goes to sq[u].
@@ -470,15 +473,14 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
   constexpr int NG = UT * (UT + 1) / 2;
   const int gq = lane >> 2, t = lane & 3;
   const int gst = U + 1;
-  float g[NG][2][4], qa[UT][2][4];
+  float g[NG][2][4];
+  float2 qf[UT];
 #pragma unroll
   for (int i = 0; i < NG; ++i)
 #pragma unroll
     for (int e = 0; e < 4; ++e) { g[i][0][e] = 0.0f; g[i][1][e] = 0.0f; }
 #pragma unroll
-  for (int i = 0; i < UT; ++i)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) { qa[i][0][e] = 0.0f; qa[i][1][e] = 0.0f; }
+  for (int i = 0; i < UT; ++i) qf[i] = make_float2(0.0f, 0.0f);
   // k-steps in chunks of KC: the loads of a chunk are issued before its
   // products, so that they are in flight together (fewer k-steps per chunk
   // for four user tiles, whose accumulators take most of the registers)
@@ -495,7 +497,7 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
         const int u = m * 8 + gq;
         hv[c][m] = (c < nc && u < U) ? hld(u, a) : make_float2(0.0f, 0.0f);
       }
-      yv[c] = (c < nc && gq == 0) ? yld(a) : make_float2(0.0f, 0.0f);
+      yv[c] = c < nc ? yld(a) : make_float2(0.0f, 0.0f);
     }
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
@@ -507,10 +509,10 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
         split_tf32(hv[c][m].y, ah[m][2], al[m][2]);
         ah[m][1] = ah[m][2] ^ 0x80000000u;
         al[m][1] = al[m][2] ^ 0x80000000u;
+        // q0: conj(h) y
+        qf[m].x = fmaf(hv[c][m].x, yv[c].x, fmaf(hv[c][m].y, yv[c].y, qf[m].x));
+        qf[m].y = fmaf(hv[c][m].x, yv[c].y, fmaf(-hv[c][m].y, yv[c].x, qf[m].y));
       }
-      uint32_t yh0, yl0, yh1, yl1;
-      split_tf32(yv[c].x, yh0, yl0);
-      split_tf32(yv[c].y, yh1, yl1);
       // round 1: hi*hi and hi*lo of every tile (independent MMAs); round 2:
       // lo*hi, added to a part round 1 updated several MMAs earlier
       int tile = 0;
@@ -521,8 +523,6 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
           mma_tf32(g[tile][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
           mma_tf32(g[tile][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
         }
-        mma_tf32(qa[m][0], ah[m][0], ah[m][1], ah[m][2], yh0, yh1);
-        mma_tf32(qa[m][1], ah[m][0], ah[m][1], ah[m][2], yl0, yl1);
       }
       tile = 0;
 #pragma unroll
@@ -530,9 +530,16 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
 #pragma unroll
         for (int n = m; n < UT; ++n, ++tile)
           mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
-        mma_tf32(qa[m][1], al[m][0], al[m][1], al[m][2], yh0, yh1);
       }
     }
+  }
+  // the quad's partial sums of q0: (t0 + t1) + (t2 + t3)
+#pragma unroll
+  for (int m = 0; m < UT; ++m) {
+    qf[m].x += __shfl_xor_sync(kFullMask, qf[m].x, 1);
+    qf[m].y += __shfl_xor_sync(kFullMask, qf[m].y, 1);
+    qf[m].x += __shfl_xor_sync(kFullMask, qf[m].x, 2);
+    qf[m].y += __shfl_xor_sync(kFullMask, qf[m].y, 2);
   }
   __syncwarp();  // every lane's reads of y are done before q0 can overwrite it
   int tile = 0;
@@ -553,8 +560,7 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
       }
     }
     const int u = m * 8 + gq;
-    if (t == 0 && u < U)  // column 0 holds q0: rows gq (re) and gq + 8 (im)
-      sq[u] = make_float2(qa[m][1][0] + qa[m][0][0], qa[m][1][2] + qa[m][0][2]);
+    if (t == 0 && u < U) sq[u] = qf[m];
   }
 }
 
