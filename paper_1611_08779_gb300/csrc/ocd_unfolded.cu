@@ -881,6 +881,7 @@ ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
   for (long long pi = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pi < npairs;
        pi += nw) {
     __syncwarp();
+    // both samples' G from the checkpoint: every copy in flight at once
     for (int h = 0; h < 2; ++h) {
       const long long s2 = 2 * pi + h;
       if (s2 >= P.samples) break;
@@ -889,8 +890,9 @@ ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
       int rws, r0, u;
       row_lane(U, lane, rws, r0, u);
       if (r0 < rws)
-        for (int i = r0; i < U; i += rws) sG[i * gst + u] = ckG[i * U + u];
+        for (int i = r0; i < U; i += rws) async_copy8(sG + i * gst + u, ckG + i * U + u);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
     const long long s = 2 * pi + hh;
     const bool valid = s < P.samples;
@@ -929,15 +931,22 @@ ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
     al_mu = half_sum(al_mu);
     float2 qbar = make_float2(0.0f, 0.0f);
     float* part = P.partial + s * 2 * K;
+    // checkpointed (q, z) of the sweep being reversed, loaded one sweep ahead
+    float2 nq = make_float2(0.0f, 0.0f), nz = nq;
+    if (act) {
+      const float2* ck = P.ckpt + ckpt_qz(P, K - 1, s);
+      nq = ck[j];
+      nz = ck[U + j];
+    }
     for (int k = K - 1; k >= 0; --k) {
       const float om = __ldg(P.omega + k);
       float d, p;
       gains(nrm, __ldg(P.alpha + k), d, p);
-      float2 q = make_float2(0.0f, 0.0f), z = q;
-      if (act) {
-        const float2* ck = P.ckpt + ckpt_qz(P, k, s);
-        q = ck[j];
-        z = ck[U + j];
+      float2 q = nq, z = nz;
+      if (k > 0 && act) {
+        const float2* ck = P.ckpt + ckpt_qz(P, k - 1, s);
+        nq = ck[j];
+        nz = ck[U + j];
       }
       float2 zb = make_float2(0.0f, 0.0f), qs = zb;
       qsweep16<true>(P, sG, gst, j, q, z, d, p, om, zb, qs);
@@ -950,31 +959,41 @@ ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
         hs.x = fmaf(g.x, qi.x, fmaf(g.y, qi.y, hs.x));
         hs.y = fmaf(g.x, qi.y, fmaf(-g.y, qi.x, hs.y));
       }
+      // The terms of this lane's user that do not depend on hs, for every
+      // lane at once; in the reverse user loop only the chain through hs
+      // stays (lane u: g = zbar - G[:, u]^H q', dq = d m om g), and the
+      // rest of user u's terms follow the loop.  Per value the operations
+      // are those of the one-sample kernel, in the same order.
+      const float wr0 = fmaf(d, qs.x, p * zb.x);
+      const float wi0 = fmaf(d, qs.y, p * zb.y);
+      float cr = wr0, ci = wi0;
+      project(cr, ci, P.D);
+      float mr = 1.0f, mi = 1.0f;
+      if (P.D.box) {
+        mr = fabsf(wr0) < P.D.box_a ? 1.0f : 0.0f;
+        mi = (!P.D.bpsk && fabsf(wi0) < P.D.box_a) ? 1.0f : 0.0f;
+      }
+      const float mor = mr * om, moi = mi * om;
+      float gr = 0.0f, gi = 0.0f;
       for (int u = U - 1; u >= 0; --u) {
-        const float2 hr = hs;  // lane u: G[:, u]^H q'
         float2 dq = make_float2(0.0f, 0.0f);
         if (j == u) {
-          const float wr0 = fmaf(d, qs.x, p * zb.x);
-          const float wi0 = fmaf(d, qs.y, p * zb.y);
-          float cr = wr0, ci = wi0;
-          project(cr, ci, P.D);
-          float mr = 1.0f, mi = 1.0f;
-          if (P.D.box) {
-            mr = fabsf(wr0) < P.D.box_a ? 1.0f : 0.0f;
-            mi = (!P.D.bpsk && fabsf(wi0) < P.D.box_a) ? 1.0f : 0.0f;
-          }
-          const float gr = zbar.x - hr.x, gi = zbar.y - hr.y;
-          om_l = fmaf(cr - zb.x, gr, fmaf(ci - zb.y, gi, om_l));
-          const float wbr = mr * om * gr, wbi = mi * om * gi;
-          zbar = make_float2(zbar.x - om * gr + p * wbr, zbar.y - om * gi + p * wbi);
-          dq = make_float2(d * wbr, d * wbi);
-          qbar = make_float2(qbar.x + dq.x, qbar.y + dq.y);
-          al_l -= d * d * fmaf(qs.x, wbr, qs.y * wbi) + p * d * fmaf(zb.x, wbr, zb.y * wbi);
+          gr = zbar.x - hs.x;  // hs of lane u: G[:, u]^H q'
+          gi = zbar.y - hs.y;
+          dq = make_float2(d * (mor * gr), d * (moi * gi));
         }
         dq = shfl2_16(dq, u);
         const float2 g = j < U ? sG[u * gst + j] : make_float2(0.0f, 0.0f);
         hs.x = fmaf(g.x, dq.x, fmaf(g.y, dq.y, hs.x));
         hs.y = fmaf(g.x, dq.y, fmaf(-g.y, dq.x, hs.y));
+      }
+      if (j < U) {
+        om_l = fmaf(cr - zb.x, gr, fmaf(ci - zb.y, gi, om_l));
+        const float wbr = mor * gr, wbi = moi * gi;
+        zbar = make_float2(zbar.x - om * gr + p * wbr, zbar.y - om * gi + p * wbi);
+        const float2 dq = make_float2(d * wbr, d * wbi);
+        qbar = make_float2(qbar.x + dq.x, qbar.y + dq.y);
+        al_l -= d * d * fmaf(qs.x, wbr, qs.y * wbi) + p * d * fmaf(zb.x, wbr, zb.y * wbi);
       }
       float om_bar = half_sum(om_l);
       float al_bar = half_sum(al_l);
