@@ -85,7 +85,7 @@ struct TcShape {
   static constexpr int kAccCol = kOpStages * kACols;
   static constexpr int kTmemCols = 512;                   // the whole TMEM of an SM
   static constexpr int kEpiG = 32 * WideShape::kGRow * 4;  // G rows (re run | im run | pad)
-  static constexpr int kEpiQ = 16 * 32 * 8;               // q0, then z, [symbol][user]
+  static constexpr int kEpiQ = 16 * WideShape::kSqRow * 4;  // q0, then z (wide_sq layout)
   static constexpr int kEpiPre = 32 * 16;                 // (d^-1, p, rho~ step^2, u scale)
   static constexpr int kEpiBytes = kEpiG + kEpiQ + kEpiPre;
   static constexpr int kEpiWarps = 8;                     // one subcarrier each per group
@@ -464,7 +464,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
         float* sq = reinterpret_cast<float*>(eb + S::kEpiG);
 #pragma unroll
         for (int t = 0; t < YR; ++t)
-          if (t < T) sq[2 * (t * 32 + lane) + part] = __uint_as_float(vq[t]);
+          if (t < T) sq[wide_sq(t, lane) + part] = __uint_as_float(vq[t]);
         // row `lane`'s run of real or imaginary parts as 8 chunks of 4 (the
         // row pad puts the lanes' rows on distinct bank positions)
         float4* row = reinterpret_cast<float4*>(sg + (part ? wide_gim(lane, 0) : wide_gre(lane, 0)));

@@ -65,10 +65,12 @@ struct WideShape {
   static constexpr int kBufBytes = kYBytes + kHBytes;       // multiple of 1024
   static constexpr int kStages = OCD_WIDE_STAGES;
   static constexpr int kUP = kUsers / 2;                    // users per sweep lane
-  // q0, later z [pass symbol][u] (8 kPass kUsers bytes) lives in the staging
-  // buffer of the step whose epilogue uses it: that buffer receives its next
-  // copy only when the following step starts
-  static constexpr int kQBytes = 8 * kPass * kUsers;
+  // q0, later z [pass symbol][u] lives in the staging buffer of the step
+  // whose epilogue uses it: that buffer receives its next copy only when the
+  // following step starts.  A symbol's row holds the 32 users' (re, im) in
+  // kSqRow floats, users 16-31 four floats further on (see wide_sq).
+  static constexpr int kSqRow = 2 * kUsers + 8;
+  static constexpr int kQBytes = 4 * kPass * kSqRow;
   static_assert(kQBytes <= kBufBytes, "q0 fits in a staging buffer");
   static constexpr int kOffG = kStages * kBufBytes;         // G [i][j]
   // floats per G row: the real run, the imaginary run and 4 floats of pad,
@@ -87,6 +89,13 @@ struct WideShape {
 __device__ __forceinline__ int wide_gre(int i, int j) { return i * WideShape::kGRow + j; }
 __device__ __forceinline__ int wide_gim(int i, int j) {
   return i * WideShape::kGRow + WideShape::kUsers + j;
+}
+// Float index of Re q0 (or z) of symbol t, user u (Im follows): rows of
+// kSqRow floats, users 16-31 shifted by four floats, so that the 32
+// consecutive floats a sweep lane (2 ts + hf) reads start at bank
+// 8 ts + 4 hf (mod 32): the lanes of a quarter warp read distinct banks.
+__host__ __device__ constexpr int wide_sq(int t, int u) {
+  return t * WideShape::kSqRow + 2 * u + (u >= 16 ? 4 : 0);
 }
 // Fault word of the wide kernels (bit 0: a wait timed out; bit 1: a batched
 // cell's tensor map was misaligned).  Defined here because exactly one
@@ -131,7 +140,7 @@ __device__ __forceinline__ void wide_outputs(const DetectParams& P, const float*
     for (int f = lane; f < ns * U; f += 32) {
       const int ts = ts0 + (full ? f >> 5 : f / U);
       const int u = f - (ts - ts0) * U;
-      const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
+      const float2 z = *reinterpret_cast<const float2*>(sq + wide_sq(ts, u));
       const long long o = (sc * T + tb + ts) * U + u;
       if (P.xhat) P.xhat[o] = z;
       if (P.llr) {
@@ -189,11 +198,13 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
     const bool act = ts < np;
     unsigned long long QR[UP / 2], QI[UP / 2];
     float zr[UP], zi[UP];
+    const float4* q4 = reinterpret_cast<const float4*>(sq + wide_sq(ts & 15, hf * UP));
 #pragma unroll
     for (int l2 = 0; l2 < UP / 2; ++l2) {
-      const int j = hf * UP + 2 * l2;
-      QR[l2] = act ? f2_pack(sq[2 * (ts * NU + j)], sq[2 * (ts * NU + j + 1)]) : 0ull;
-      QI[l2] = act ? f2_pack(sq[2 * (ts * NU + j) + 1], sq[2 * (ts * NU + j + 1) + 1]) : 0ull;
+      // users hf UP + 2 l2 and + 1: (re, im, re, im)
+      const float4 v = act ? q4[l2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      QR[l2] = f2_pack(v.x, v.z);
+      QI[l2] = f2_pack(v.y, v.w);
       zr[2 * l2] = zr[2 * l2 + 1] = 0.0f;
       zi[2 * l2] = zi[2 * l2 + 1] = 0.0f;
     }
@@ -248,12 +259,10 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
     }
     __syncwarp();
     if (act) {
+      float4* z4 = reinterpret_cast<float4*>(sq + wide_sq(ts, hf * UP));
 #pragma unroll
-      for (int l = 0; l < UP; ++l) {
-        const int j = hf * UP + l;
-        sq[2 * (ts * NU + j)] = zr[l];
-        sq[2 * (ts * NU + j) + 1] = zi[l];
-      }
+      for (int l2 = 0; l2 < UP / 2; ++l2)
+        z4[l2] = make_float4(zr[2 * l2], zi[2 * l2], zr[2 * l2 + 1], zi[2 * l2 + 1]);
     }
     __syncwarp();
   }
@@ -267,8 +276,8 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
 #pragma unroll
     for (int l = 0; l < UP; ++l) {
       const int j = hf * UP + l;
-      qr[l] = act ? sq[2 * (ts * NU + j)] : 0.0f;
-      qi[l] = act ? sq[2 * (ts * NU + j) + 1] : 0.0f;
+      qr[l] = act ? sq[wide_sq(ts, j)] : 0.0f;
+      qi[l] = act ? sq[wide_sq(ts, j) + 1] : 0.0f;
       zr[l] = 0.0f;
       zi[l] = 0.0f;
     }
@@ -316,8 +325,8 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
 #pragma unroll
       for (int l = 0; l < UP; ++l) {
         const int j = hf * UP + l;
-        sq[2 * (ts * NU + j)] = zr[l];
-        sq[2 * (ts * NU + j) + 1] = zi[l];
+        sq[wide_sq(ts, j)] = zr[l];
+        sq[wide_sq(ts, j) + 1] = zi[l];
       }
     }
     __syncwarp();
@@ -599,8 +608,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
           const int ts = 8 * n + 2 * t + e;
           const int u = m * 8 + gq;
           const float (&a)[2][4] = acc[2 * m + n];
-          sq[2 * (ts * NU + u)] = a[1][e] + a[0][e];
-          sq[2 * (ts * NU + u) + 1] = a[1][2 + e] + a[0][2 + e];
+          sq[wide_sq(ts, u)] = a[1][e] + a[0][e];
+          sq[wide_sq(ts, u) + 1] = a[1][2 + e] + a[0][2 + e];
         }
     __syncwarp();
     wide_sweeps_outputs(P, sq, sg, spre, sc, tb, np);
