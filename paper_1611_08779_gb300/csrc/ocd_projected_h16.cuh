@@ -48,7 +48,7 @@ struct H16Shape {
   static constexpr int kStages = OCD_H16_STAGES;
   static constexpr int kUP = kUsers / 2;                   // users per sweep lane
   static constexpr int kOffQ = kStages * kBufBytes;        // q0, later z [pass symbol][u]
-  static constexpr int kOffG = kOffQ + 8 * kPass * kUsers;
+  static constexpr int kOffG = kOffQ + 4 * kPass * SqLayout<kUsers>::kRow;
   static constexpr int kOffPre = kOffG + 8 * kUsers * kUsers;
   static constexpr int kOffBar = kOffPre + 16 * kUsers;
   static constexpr int kWarpBytes = ((kOffBar + 8 * kStages + 1023) / 1024) * 1024;
@@ -267,8 +267,8 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
         for (int e = 0; e < 2; ++e) {
           const int ts = 8 * n + 2 * t + e;
           const int u = m * 8 + gq;
-          sq[2 * (ts * NU + u)] = qacc[m][n][e];
-          sq[2 * (ts * NU + u) + 1] = qacc[m][n][2 + e];
+          sq[tma_sq<NU>(ts, u)] = qacc[m][n][e];
+          sq[tma_sq<NU>(ts, u) + 1] = qacc[m][n][2 + e];
         }
     if (first) {
 #pragma unroll
@@ -307,13 +307,19 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       const int hf = lane & 1;
       const bool act = ts < np;
       float qr[UP], qi[UP], zr[UP], zi[UP];
+      {
+        // this lane's half of symbol ts: UP users as (re, im) pairs
+        const float4* q4 = reinterpret_cast<const float4*>(sq + tma_sq<NU>(ts & 15, hf * UP));
 #pragma unroll
-      for (int l = 0; l < UP; ++l) {
-        const int j = hf * UP + l;
-        qr[l] = act ? sq[2 * (ts * NU + j)] : 0.0f;
-        qi[l] = act ? sq[2 * (ts * NU + j) + 1] : 0.0f;
-        zr[l] = 0.0f;
-        zi[l] = 0.0f;
+        for (int l2 = 0; l2 < UP / 2; ++l2) {
+          const float4 v = act ? q4[l2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          qr[2 * l2] = v.x;
+          qi[2 * l2] = v.y;
+          qr[2 * l2 + 1] = v.z;
+          qi[2 * l2 + 1] = v.w;
+          zr[2 * l2] = zr[2 * l2 + 1] = 0.0f;
+          zi[2 * l2] = zi[2 * l2 + 1] = 0.0f;
+        }
       }
       float dv[NU], pv[NU];
 #pragma unroll
@@ -357,12 +363,10 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       }
       __syncwarp();
       if (act) {
+        float4* z4 = reinterpret_cast<float4*>(sq + tma_sq<NU>(ts, hf * UP));  // z overwrites q0
 #pragma unroll
-        for (int l = 0; l < UP; ++l) {
-          const int j = hf * UP + l;
-          sq[2 * (ts * NU + j)] = zr[l];
-          sq[2 * (ts * NU + j) + 1] = zi[l];
-        }
+        for (int l2 = 0; l2 < UP / 2; ++l2)
+          z4[l2] = make_float4(zr[2 * l2], zi[2 * l2], zr[2 * l2 + 1], zi[2 * l2 + 1]);
       }
       __syncwarp();
     }
@@ -378,7 +382,7 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
       for (int f = lane; f < np * U; f += 32) {
         const int ts = full_tile ? f / NU : f / U;
         const int u = f - ts * U;
-        const float2 z = make_float2(sq[2 * (ts * NU + u)], sq[2 * (ts * NU + u) + 1]);
+        const float2 z = *reinterpret_cast<const float2*>(sq + tma_sq<NU>(ts, u));
         const long long o = (sc * T + tb + ts) * U + u;
         if (P.xhat) P.xhat[o] = z;
         if (P.llr) {

@@ -15,6 +15,26 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
+// Per-warp q0 / z buffer of the 8- and 16-user bulk-copy kernels: float
+// index of Re of symbol t, user u (Im follows).  Rows of kRow floats, the
+// users of the second sweep half kHalf floats further on, chosen so that
+// the 16-byte runs of the sweep lanes 2 ts + hf of a quarter warp (base
+// kRow ts + NU hf + kHalf hf) start on distinct banks.
+template <int NU>
+struct SqLayout;
+template <>
+struct SqLayout<8> {
+  static constexpr int kRow = 24, kHalf = 4;
+};
+template <>
+struct SqLayout<16> {
+  static constexpr int kRow = 36, kHalf = 0;
+};
+template <int NU>
+__host__ __device__ constexpr int tma_sq(int t, int u) {
+  return t * SqLayout<NU>::kRow + 2 * u + (u >= NU / 2 ? SqLayout<NU>::kHalf : 0);
+}
+
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
