@@ -28,8 +28,8 @@
 //               a ring of raw stages;
 //   warps 2-5   transform, one per TMEM lane quarter: a thread (= user)
 //               writes its Re- or Im-row, hi and lo, into the A stage with
-//               tcgen05.st; the Re warps also store their rows into B, the
-//               Im warps copy the received rows with their lo rows;
+//               tcgen05.st; the Re warps also store their rows into B, and
+//               all four copy a share of the received rows with their lo rows;
 //   warp 1      one thread issues 3 MMAs per K slice (A from TMEM) into the
 //               pair's TMEM slot and commits each block (the stage is free
 //               again) and each pair (accumulators ready);
@@ -333,7 +333,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
     // Warp with TMEM lane quarter q writes A rows 32q + u (u = lane): the
     // Re-row (q < 2) or the Im-row (q >= 2) of user u of half h = q & 1,
     // hi and lo, with tcgen05.st.  The Re warps also store their rows into
-    // B (the G columns), the Im warps copy the received rows of their half.
+    // B (the G columns); the received rows are copied by all four.
     // An absent half b transforms stale data into rows nobody reads.
     const int q = warp & 3;
     const int h = q & 1;
@@ -399,16 +399,16 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
             *reinterpret_cast<float4*>(lo + o1) = make_float4(w[4], w[5], w[6], w[7]);
           }
         }
-        if (imrow) {
-          // received rows of half h, as staged (the same swizzled layout, the
-          // same 1024-byte phase) and their lo parts
-          const unsigned char* ys = rawst + h * S::kRawY;
-          const int yo = h * S::kRawY;
+        {
+          // received rows of both halves, as staged (the same swizzled layout,
+          // the same 1024-byte phase) and their lo parts: the 16-byte chunks
+          // shared out over the four transform warps
+          const int tt = 32 * (q ^ 2) + lane;  // 0 .. 127
 #pragma unroll
-          for (int c = lane; c < YR * 8; c += 32) {
-            const float4 x = *reinterpret_cast<const float4*>(ys + 16 * c);
-            *reinterpret_cast<float4*>(hi + yo + 16 * c) = x;
-            *reinterpret_cast<float4*>(lo + yo + 16 * c) = tf32_lo4(x);
+          for (int c = tt; c < 2 * YR * 8; c += 32 * NTW) {
+            const float4 x = *reinterpret_cast<const float4*>(rawst + 16 * c);
+            *reinterpret_cast<float4*>(hi + 16 * c) = x;
+            *reinterpret_cast<float4*>(lo + 16 * c) = tf32_lo4(x);
           }
         }
         tmem_wait_st();
