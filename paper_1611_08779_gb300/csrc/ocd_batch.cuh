@@ -47,6 +47,11 @@ BatchFn batched_tma_kernel(int U);
 cudaError_t encode_ymap(const DetectParams& P, CUtensorMap* map);
 // The same with a box of `rows` received rows (16 antennas wide).
 cudaError_t encode_ymap_rows(const DetectParams& P, CUtensorMap* map, int rows);
+// Y's tensor map for the 8/16-user bulk-copy kernel: the 3-D view (32
+// floats of 16 antennas, rows, 16-antenna chunks; one copy fetches both
+// chunks of a 32-antenna block) when B is a multiple of 16, else the 2-D
+// view; *is3d tells which (it goes to DetectParams::ymap3d).
+cudaError_t encode_ymap_tma(const DetectParams& P, CUtensorMap* map, int* is3d);
 // Staged steps (antenna blocks x symbol passes) per subcarrier of the
 // bulk-copy kernels.
 int tma_steps_per_sc(int B, int T);

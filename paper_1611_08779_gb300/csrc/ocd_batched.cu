@@ -266,7 +266,10 @@ int plan_batch(const ocd_cell_t* cells, int ncells, const ocd_tune_t* tune,
         ocd::BatchCell& bc = L.tab->cell[k - a];
         bc.P = cp.P;
         if (cp.kind == 1) {
-          const cudaError_t e = ocd::encode_ymap(cp.P, &bc.ymap);
+          // the 8/16-user bulk-copy kernel takes the 3-D view where B allows;
+          // the 32-user kernel copies 16-antenna boxes (2-D view)
+          const cudaError_t e = cp.ut == 4 ? ocd::encode_ymap(cp.P, &bc.ymap)
+                                           : ocd::encode_ymap_tma(cp.P, &bc.ymap, &bc.P.ymap3d);
           if (e == cudaErrorNotSupported)
             return fail(OCD_ERR_UNSUPPORTED, "cell %d: no tensor-map encoder in this driver", cp.index);
           if (e != cudaSuccess) return fail(OCD_ERR_CUDA, "cell %d: tensor map encoding failed", cp.index);

@@ -40,6 +40,7 @@ struct DetectParams {
   int vec_y;        // Y rows may be read with 16-byte loads
   unsigned long long wait_ns;  // limit of any wait for a copy engine (ns)
   int storage;      // Storage of H and Y
+  int ymap3d;       // bulk-copy kernel: Y's tensor map is the 3-D view (one copy per 32 antennas)
 };
 
 // Converting loads of complex element `idx` of a [.. ] array in `storage`.

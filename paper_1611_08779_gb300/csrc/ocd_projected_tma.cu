@@ -56,11 +56,35 @@ cudaError_t encode_ymap_rows(const DetectParams& P, CUtensorMap* map, int rows) 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t encode_ymap_tma(const DetectParams& P, CUtensorMap* map, int* is3d) {
+  *is3d = 0;
+  if (P.B % TmaShape<1>::kBoxAnt != 0) return encode_ymap(P, map);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // dims: 32 floats (16 antennas) of a chunk, rows (subcarrier, symbol),
+  // chunks; the box fetches a whole 32-antenna block, laid out chunk by
+  // chunk exactly as two 2-D boxes would be
+  constexpr int kChunk = 2 * TmaShape<1>::kBoxAnt;
+  const cuuint64_t dims[3] = {(cuuint64_t)kChunk, (cuuint64_t)P.Nsc * (cuuint64_t)P.T,
+                              2ull * (cuuint64_t)P.B / kChunk};
+  const cuuint64_t strides[2] = {2ull * (cuuint64_t)P.B * sizeof(float), kChunk * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)TmaShape<1>::kPass,
+                             (cuuint32_t)TmaShape<1>::kBoxes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(P.Y), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return encode_ymap(P, map);  // the 2-D view always encodes
+  *is3d = 1;
+  return cudaSuccess;
+}
+
 cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStream_t stream) {
   CUtensorMap map;
-  const cudaError_t e = encode_ymap(P, &map);
-  if (e != cudaSuccess) return e;
   DetectParams p = P;
+  const cudaError_t e = encode_ymap_tma(P, &map, &p.ymap3d);
+  if (e != cudaSuccess) return e;
   void* args[] = {&p, &map};
   return cudaLaunchKernel(projected_tma_kernel_ptr(P.U), dim3(grid), dim3(projected_tma_threads()),
                           args, projected_tma_smem_per_cta(P.U), stream);

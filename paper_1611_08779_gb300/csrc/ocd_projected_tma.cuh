@@ -165,12 +165,18 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
     const uint32_t bar = bar0 + 8 * buf;
     unsigned char* bp = ws + buf * S::kBufBytes;
     const int nbox = (bb + S::kBoxAnt - 1) / S::kBoxAnt;
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(nbox * S::kBoxBytes + bb * U * 8));
+    // the 3-D view fetches the block's two 16-antenna chunks in one copy (a
+    // chunk past B arrives as zeros and still counts)
+    const uint32_t ybytes = P.ymap3d ? (uint32_t)S::kYBytes : (uint32_t)(nbox * S::kBoxBytes);
+    if (lane == 0) mbar_expect_tx(bar, ybytes + (uint32_t)(bb * U * 8));
     __syncwarp();
     fence_proxy_async();
-    if (lane < nbox)
+    if (P.ymap3d) {
+      if (lane == 0) tma_load_3d(smem_addr(bp), ymap, 0, (int)(q.sc * T + tb), b0 / S::kBoxAnt, bar);
+    } else if (lane < nbox) {
       tma_load_2d(smem_addr(bp + lane * S::kBoxBytes), ymap, 2 * (b0 + S::kBoxAnt * lane),
                   (int)(q.sc * T + tb), bar);
+    }
     if (lane == 31) {
       const float2* src = P.H + (q.sc * (long long)B + b0) * U;
       bulk_g2s(smem_addr(bp + S::kYBytes), src, (uint32_t)(bb * U * 8), bar);
