@@ -64,11 +64,11 @@ typedef enum { OCD_MMSE = 0, OCD_BOX = 1 } ocd_mode_t;
  *                       16-byte aligned H and Y; else RESIDUAL.
  * For T == 1 and U <= 8 (float32 storage, even B, 16-byte aligned H and Y)
  * the projected form runs with one lane per subcarrier (G and q0 accumulated
- * in registers, no reduction across lanes).  For 16 < U <= 32 and 9 <= T <= 16
+ * in registers, no reduction across lanes).  For 16 < U <= 32 and T <= 16
  * (float32 storage, even B, 16-byte aligned H and Y) its two products run on
  * the fifth-generation tensor cores with accumulators in tensor memory (one
- * CTA per SM, holding that SM's whole tensor memory while it runs); for the
- * other shapes the warp-level tensor-core kernels are the faster ones.
+ * CTA per SM, holding that SM's whole tensor memory while it runs); the other
+ * shapes run warp-level tensor-core kernels.
  *   OCD_ALGO_PROJECTED_WARP  the projected form with warp-level tensor-core
  *                       products only.
  *   OCD_ALGO_PROJECTED_TC    the projected form with the tensor-memory kernel
@@ -193,8 +193,11 @@ int ocd_wait_selftest(int limit_us, cudaStream_t stream);
  * problems with different B, U, Nsc, T, K, mode and alphabet.  The batched
  * entry points detect a list of such problems ("cells") with persistent
  * kernels that draw their work from device ticket counters (atomicAdd only;
- * no kernel waits on another block); cells with 17-32 users and 9-16 symbols
- * in the projected form run the tensor-memory kernel in a launch of their own.
+ * no kernel waits on another block); cells with 17-32 users and 9-16
+ * symbols in the projected form run the tensor-memory kernel in a launch of
+ * their own (by default: a tensor-memory launch holds whole SMs, which the
+ * other cells' launches would share; PROJECTED_TC or a tune entry asks for
+ * it at any T <= 16, PROJECTED_WARP not at all).
  * Each cell's results are those of ocd_detect_typed with the same arguments
  * in the same arrangement.
  * ------------------------------------------------------------------------- */

@@ -226,12 +226,20 @@ bool can_wide(const ocd::DetectParams& P) {
 bool can_tc(const ocd::DetectParams& P) {
   return can_wide(P) && P.T <= ocd::kTcMaxSymbols;
 }
-// Where the projected form takes the tcgen05 kernel by default: measured
-// faster than the warp-level kernel for 9..16 symbols (256x32, T = 14: 0.251
-// against 0.262 ms); at T <= 8 the warp-level kernel, which then folds q0 into
-// its G phase, is faster (T = 7: 0.190 against 0.225 ms; T = 1: 0.667 against
-// 0.760 ms).
-bool prefer_tc(const ocd::DetectParams& P) { return can_tc(P) && P.T > 8; }
+// Where the projected form takes the tcgen05 kernel by default: wherever it
+// fits (T <= 16).  Measured faster than the warp-level kernel at every shape
+// timed, including the short passes where the warp-level kernel folds q0
+// into its G phase (256x32: T = 14 0.181 against 0.239 ms, T = 7 0.170
+// against 0.181, T = 1 0.588 against 0.666; 128x32 T = 1 0.638 against
+// 0.780; 32x17 T = 5 0.343 against 0.355).
+bool prefer_tc(const ocd::DetectParams& P) { return can_tc(P); }
+// The same choice for a cell of the batched form, where a tcgen05 launch
+// holds whole SMs (all of their shared and tensor memory) while the other
+// cells' persistent launches would share them: only for 9..16 symbols.  On
+// the 24-cell mix of the benchmark, the tcgen05 kernel for the 256x32 cells
+// with 1 and 7 symbols made the batch 6% slower (0.504 -> 0.535 ms) although
+// each of those cells alone is faster on it.
+bool prefer_tc_batched(const ocd::DetectParams& P) { return can_tc(P) && P.T > 8; }
 // One lane per subcarrier: one symbol, float32 storage, U <= 8, even B,
 // 16-byte aligned bases.
 bool can_lane(const ocd::DetectParams& P) {

@@ -115,8 +115,9 @@ int plan_cell(const ocd_cell_t& c, int index, const ocd_tune_t* tune,
     cp.work = (double)c.Nsc * (8.0 * c.B * c.U + 8.0 * c.B + 12.0 * c.U);
     return OCD_OK;
   }
-  if (algo == OCD_ALGO_PROJECTED && (use_tc || (!warp_only && prefer_tc(cp.P)))) {
-    // 17-32 users, 9-16 symbols: the single-problem path's tcgen05 kernel,
+  if (algo == OCD_ALGO_PROJECTED && (use_tc || (!warp_only && prefer_tc_batched(cp.P)))) {
+    // 17-32 users, 9-16 symbols by default (any T <= 16 when asked for): the
+    // single-problem path's tcgen05 kernel,
     // launched for this cell alone (one CTA per SM, same results)
     cp.kind = 3;
     cp.ut = 4;
@@ -634,6 +635,32 @@ int ocd_autotune_batched(const ocd_cell_t* cells, int ncells, void* workspace,
     if (st == OCD_OK && us < kKeep * best) {
       out = def;
       best = us;
+    }
+    // one kernel for every 17-32-user shape at once (their launches share
+    // the SMs with each other, so single changes can each stay under the
+    // margin while the joint one does not)
+    for (int a : {OCD_ALGO_PROJECTED_WARP, OCD_ALGO_PROJECTED_TC}) {
+      if (st != OCD_OK) break;
+      ocd_tune_t trial = out;
+      int changed = 0;
+      for (int i = 0; i < trial.n; ++i) {
+        ocd_tune_entry_t& t = trial.entry[i];
+        const bool proj = t.algo == OCD_ALGO_PROJECTED || t.algo == OCD_ALGO_PROJECTED_WARP ||
+                          t.algo == OCD_ALGO_PROJECTED_TC;
+        if (shapes[i].wide && shapes[i].tc_all && proj && t.algo != a) {
+          t.algo = a;
+          t.time_us = 0.0f;
+          ++changed;
+        }
+      }
+      if (changed < 2) continue;  // a single shape is tried below
+      const int s2 = time_run(cells, ncells, &trial, nullptr, us);
+      if (s2 == OCD_ERR_UNSUPPORTED) continue;
+      if (s2 != OCD_OK) { st = s2; break; }
+      if (us < kKeep * best) {
+        out = trial;
+        best = us;
+      }
     }
     for (int i = 0; i < out.n && st == OCD_OK; ++i) {
       const Shape& sh = shapes[i];

@@ -54,7 +54,8 @@ bool can_tma32(const ocd::DetectParams& P);  // U <= 16
 bool can_lane(const ocd::DetectParams& P);   // T == 1, U <= 8: one lane per subcarrier
 bool can_wide(const ocd::DetectParams& P);   // 16 < U <= 32
 bool can_tc(const ocd::DetectParams& P);     // the tcgen05 kernel supports the shape
-bool prefer_tc(const ocd::DetectParams& P);  // ... and is the projected default
+bool prefer_tc(const ocd::DetectParams& P);
+bool prefer_tc_batched(const ocd::DetectParams& P);  // ... the default for a batched cell  // ... and is the projected default
 
 // Grid of the one-lane-per-subcarrier kernel for P (0 when it cannot be
 // resident on the device).

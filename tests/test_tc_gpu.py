@@ -84,9 +84,9 @@ def test_more_than_16_symbols():
 
 
 def test_default_projected_form_matches_the_oracle_on_both_sides_of_the_switch():
-    """The library's own choice (tensor-memory kernel for 9..16 symbols,
-    warp-level kernel below) at T = 8 and T = 9."""
-    for T in (8, 9):
+    """The library's own choice (tensor-memory kernel up to 16 symbols,
+    warp-level kernel above) at T = 1, 8, 16 and 17."""
+    for T in (1, 8, 16, 17):
         d = synth.make_uplink(30, 128, 32, T, 64, 16.0, 98 + T)
         x, L = run(d, 3, orc.MMSE, 64, "projected")
         assert_parity(x, L, d["H"], d["Y"], d["N0"], 1.0, 3, orc.MMSE, 64, f"T={T}")
