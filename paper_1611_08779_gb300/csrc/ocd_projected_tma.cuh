@@ -17,7 +17,11 @@
 //     the realified K = 2B dimension with the three-term TF32 split, which
 //     keeps FP32-level accuracy.  A holds [Re H^H; Im H^H] for the 8 user
 //     slots; B is a staged received row (interleaved re/im is exactly the
-//     K layout) or, for G, the same channel entries that form A.
+//     K layout) or, for G, the same channel entries that form A.  A
+//     diagonal G tile runs two of the three split products: its lo*hi term
+//     is the conjugate transpose of its hi*lo term (products of TF32 values
+//     are exact and both sums run over the same k order, so the transposed
+//     entry is bit for bit the sum an MMA would give).
 //   Epilogue (last block of a pass): the accumulator fragments go to shared
 //     memory; the first pass also derives ||h_u||^2 = G_uu, d_u^-1, p_u and
 //     the soft-output constants; the K sweeps run with two lanes per symbol;
@@ -300,8 +304,17 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
           // lane's A entries of user tile n (b0 = Re, b1 = Im).
           if (decltype(with_g)::value) {
 #pragma unroll
-            for (int n = m; n < UT; ++n)
-              mma3_tf32(gacc[m == 0 ? n : 2], ah[m], al[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+            for (int n = m; n < UT; ++n) {
+              if (n == m) {
+                // diagonal tile: hi*hi and hi*lo only; its lo*hi is the
+                // conjugate transpose of hi*lo (same exact products, same
+                // order: taken in the epilogue, bit for bit the same sums)
+                mma_tf32(gacc[m == 0 ? n : 2][0], ah[m][0], ah[m][1], ah[m][2], ah[n][0], ah[n][2]);
+                mma_tf32(gacc[m == 0 ? n : 2][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
+              } else {
+                mma3_tf32(gacc[m == 0 ? n : 2], ah[m], al[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+              }
+            }
           }
         }
       } else {
@@ -406,6 +419,31 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
               (a[NQ - 1][2 + e] + (NQ == 3 ? a[1][2 + e] : 0.0f)) + a[0][2 + e];
         }
     if (first) {
+      // lo*hi of a diagonal G tile: lo*hi[i][j] = conj(hi*lo[j][i]); the
+      // hi*lo parts go to G's buffer first, then each lane reads the entry
+      // transposed to its own
+      float lhr[UT][2] = {}, lhi[UT][2] = {};
+      if constexpr (NQ == 3) {
+#pragma unroll
+        for (int m = 0; m < UT; ++m)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float (&a)[NQ][4] = gacc[m == 0 ? m : 2];
+            const int i = m * 8 + gq, j = m * 8 + 2 * t + e;
+            sg[tma_gre<NU>(i, j)] = a[1][e];
+            sg[tma_gim<NU>(i, j)] = a[1][2 + e];
+          }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < UT; ++m)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int i = m * 8 + gq, j = m * 8 + 2 * t + e;
+            lhr[m][e] = sg[tma_gre<NU>(j, i)];
+            lhi[m][e] = -sg[tma_gim<NU>(j, i)];
+          }
+        __syncwarp();
+      }
 #pragma unroll
       for (int m = 0; m < UT; ++m)
 #pragma unroll
@@ -413,8 +451,11 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const float (&a)[NQ][4] = gacc[m == 0 ? n : 2];
-            const float re = (a[NQ - 1][e] + (NQ == 3 ? a[1][e] : 0.0f)) + a[0][e];
-            const float im = (a[NQ - 1][2 + e] + (NQ == 3 ? a[1][2 + e] : 0.0f)) + a[0][2 + e];
+            const bool diag3 = NQ == 3 && n == m;
+            const float lr = diag3 ? lhr[m][e] : a[NQ - 1][e];
+            const float li = diag3 ? lhi[m][e] : a[NQ - 1][2 + e];
+            const float re = (lr + (NQ == 3 ? a[1][e] : 0.0f)) + a[0][e];
+            const float im = (li + (NQ == 3 ? a[1][2 + e] : 0.0f)) + a[0][2 + e];
             const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
             sg[tma_gre<NU>(i, j)] = re;
             sg[tma_gim<NU>(i, j)] = im;

@@ -500,10 +500,12 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
 #pragma unroll
             for (int n = m; n < 4; ++n)
               mma2_round1(acc[wide_gtile(m, n)], ah[m], ah[n][0], ah[n][2], al[n][0], al[n][2]);
+          // lo*hi only off the diagonal: a diagonal tile's lo*hi is the
+          // conjugate transpose of its hi*lo (taken in the G epilogue)
 #pragma unroll
           for (int m = 0; m < 4; ++m)
 #pragma unroll
-            for (int n = m; n < 4; ++n)
+            for (int n = m + 1; n < 4; ++n)
               mma2_round2(acc[wide_gtile(m, n)], al[m], ah[n][0], ah[n][2]);
           if constexpr (FUSED) {  // q0 of symbols 0-7 from the same fragments
             const float2 ya = *reinterpret_cast<const float2*>(bp + box * S::kBoxBytes + yoff[kk]);
@@ -552,6 +554,28 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
 
     if (phase == 0) {
       // ---------------- G epilogue: Hermitian fill and preprocessing ------
+      // diagonal tiles: lo*hi[i][j] = conj(hi*lo[j][i]), read back from G's
+      // buffer after the hi*lo parts are written there
+      float lhr[4][2], lhi[4][2];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float (&a)[2][4] = acc[wide_gtile(m, m)];
+          const int i = m * 8 + gq, j = m * 8 + 2 * t + e;
+          sg[wide_gre(i, j)] = a[1][e];
+          sg[wide_gim(i, j)] = a[1][2 + e];
+        }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int i = m * 8 + gq, j = m * 8 + 2 * t + e;
+          lhr[m][e] = sg[wide_gre(j, i)];
+          lhi[m][e] = -sg[wide_gim(j, i)];
+        }
+      __syncwarp();
 #pragma unroll
       for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -559,8 +583,8 @@ __device__ __forceinline__ bool wide_walk(const DetectParams& P, const CUtensorM
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const float (&a)[2][4] = acc[wide_gtile(m, n)];
-            const float re = a[1][e] + a[0][e];
-            const float im = a[1][2 + e] + a[0][2 + e];
+            const float re = (n == m ? a[1][e] + lhr[m][e] : a[1][e]) + a[0][e];
+            const float im = (n == m ? a[1][2 + e] + lhi[m][e] : a[1][2 + e]) + a[0][2 + e];
             const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
             sg[wide_gre(i, j)] = re;
             sg[wide_gim(i, j)] = im;

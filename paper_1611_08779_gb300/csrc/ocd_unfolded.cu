@@ -460,7 +460,8 @@ __device__ __forceinline__ void qsweep(const UnfoldParams& P, const float2* sG, 
 // G: realified m16n8k8 TF32 MMAs with the two-part split (hi*hi, hi*lo +
 // lo*hi; FP32-level accuracy).  A k-step covers antennas 4s + t (lane t of a
 // quad): A = [Re H^H; Im H^H] of user tile m, B = the same entries of user
-// tile n.  q0 (one received vector: an MMA would use one column of eight)
+// tile n; a diagonal tile skips its lo*hi MMA, the conjugate transpose of
+// its hi*lo.  q0 (one received vector: an MMA would use one column of eight)
 // by FP32 fmas on the same channel entries: lane (gq, t) sums
 // conj(h_{a,u}) y_a over its antennas a = t mod 4 in order, then the four
 // lanes of a quad add up as a tree.  UT = user tiles.
@@ -524,12 +525,14 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
           mma_tf32(g[tile][1], ah[m][0], ah[m][1], ah[m][2], al[n][0], al[n][2]);
         }
       }
+      // lo*hi off the diagonal only: a diagonal tile's lo*hi is the
+      // conjugate transpose of its hi*lo (taken below)
       tile = 0;
 #pragma unroll
       for (int m = 0; m < UT; ++m) {
 #pragma unroll
         for (int n = m; n < UT; ++n, ++tile)
-          mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
+          if (n != m) mma_tf32(g[tile][1], al[m][0], al[m][1], al[m][2], ah[n][0], ah[n][2]);
       }
     }
   }
@@ -542,6 +545,32 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
     qf[m].y += __shfl_xor_sync(kFullMask, qf[m].y, 2);
   }
   __syncwarp();  // every lane's reads of y are done before q0 can overwrite it
+  // diagonal tiles: lo*hi[i][j] = conj(hi*lo[j][i]), read back from sG after
+  // the hi*lo parts are written there
+  float lhr[UT][2], lhi[UT][2];
+  {
+    int tile = 0;
+#pragma unroll
+    for (int m = 0; m < UT; ++m) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int i = m * 8 + gq, j = m * 8 + 2 * t + e;
+        if (i < U && j < U) sG[i * gst + j] = make_float2(g[tile][1][e], g[tile][1][2 + e]);
+      }
+      tile += UT - m;  // index of the next diagonal tile
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < UT; ++m)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int i = m * 8 + gq, j = m * 8 + 2 * t + e;
+        const float2 v = (i < U && j < U) ? sG[j * gst + i] : make_float2(0.0f, 0.0f);
+        lhr[m][e] = v.x;
+        lhi[m][e] = -v.y;
+      }
+    __syncwarp();
+  }
   int tile = 0;
 #pragma unroll
   for (int m = 0; m < UT; ++m) {
@@ -551,8 +580,8 @@ __device__ __forceinline__ void gram_q0_tf32_impl(HL hld, YL yld, float2* sq, fl
       for (int e = 0; e < 2; ++e) {
         const int i = m * 8 + gq, j = n * 8 + 2 * t + e;
         if (i < U && j < U) {
-          float re = g[tile][1][e] + g[tile][0][e];
-          float im = g[tile][1][2 + e] + g[tile][0][2 + e];
+          float re = (n == m ? g[tile][1][e] + lhr[m][e] : g[tile][1][e]) + g[tile][0][e];
+          float im = (n == m ? g[tile][1][2 + e] + lhi[m][e] : g[tile][1][2 + e]) + g[tile][0][2 + e];
           if (i == j) im = 0.0f;  // G_uu is real
           sG[i * gst + j] = make_float2(re, im);
           if (n != m) sG[j * gst + i] = make_float2(re, -im);
