@@ -56,6 +56,9 @@ class UnfoldedOCD(torch.autograd.Function):
         _native.check(st)
         ctx.save_for_backward(omega, alpha, H, N0, xhat, ckpt)
         ctx.args = (float(Es), _mode(mode), int(qam_order), code)
+        # an output the loss does not use gets no zero-filled gradient: its
+        # adjoint pointer goes to the library as NULL
+        ctx.set_materialize_grads(False)
         return xhat, llr
 
     @staticmethod
