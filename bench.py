@@ -122,6 +122,14 @@ class ClockSampler:
             self.reader.start()
         except (OSError, ValueError):
             self.proc = None
+        # nvidia-smi's start-up (NVML initialization, first queries) competes
+        # with the host side of the launches: the timed region starts only
+        # after its first sample has arrived (at most 5 s)
+        t0 = time.monotonic()
+        while self.proc is not None and not self.lines and time.monotonic() - t0 < 5.0:
+            if self.proc.poll() is not None:
+                break
+            time.sleep(0.02)
         time.sleep(0.3)
         return self
 
