@@ -499,7 +499,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
           sg[wide_gim(lane, lane)] = 0.0f;  // G_uu is real
         }
         __syncwarp();
-        wide_sweeps_outputs(P, sq, sg, spre, first + i * stride, 0, T);
+        wide_sweeps_outputs<false>(P, sq, sg, spre, first + i * stride, 0, T);
       }
       TC_ADD(2, c3);
     }

@@ -511,40 +511,47 @@ __device__ __forceinline__ bool tma_walk(const DetectParams& P, const CUtensorMa
       // mode (identity) and 0 on the imaginary axis for BPSK in BOX mode.
       const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
       const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
-      for (int k = 0; k < P.K; ++k) {
+      // a full user tile (U equal to the tile) needs no per-user guard: the
+      // updates of all users form one block the scheduler can interleave
+      auto sweeps = [&](auto fullc) {
+        constexpr bool FULL = decltype(fullc)::value;
+        for (int k = 0; k < P.K; ++k) {
 #pragma unroll
-        for (int u = 0; u < NU; ++u) {
-          if (u < U) {
-            const int lu = u % UP;  // compile-time slot of user u
-            const int oh = u / UP;  // half that owns user u
-            // z_u <- proj(d_u^-1 q_u + p_u z_u), dz = z_new - z_old (owner lane)
-            float wr = fmaf(dv[u], qr[lu], pv[u] * zr[lu]);
-            float wi = fmaf(dv[u], qi[lu], pv[u] * zi[lu]);
-            wr = fminf(fmaxf(wr, -are), are);
-            wi = fminf(fmaxf(wi, -aim), aim);
-            const float dr0 = wr - zr[lu];
-            const float di0 = wi - zi[lu];
-            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
-            const int owner = (lane & ~1) | oh;
-            const float dr = __shfl_sync(kFullMask, dr0, owner);
-            const float di = __shfl_sync(kFullMask, di0, owner);
-            // q <- q - G[:, u] dz for my users, with G[j][u] = conj(G[u][j])
-            const float4* gre = reinterpret_cast<const float4*>(sg + tma_gre<NU>(u, hf * UP));
-            const float4* gim = reinterpret_cast<const float4*>(sg + tma_gim<NU>(u, hf * UP));
+          for (int u = 0; u < NU; ++u) {
+            if (FULL || u < U) {
+              const int lu = u % UP;  // compile-time slot of user u
+              const int oh = u / UP;  // half that owns user u
+              // z_u <- proj(d_u^-1 q_u + p_u z_u), dz = z_new - z_old (owner lane)
+              float wr = fmaf(dv[u], qr[lu], pv[u] * zr[lu]);
+              float wi = fmaf(dv[u], qi[lu], pv[u] * zi[lu]);
+              wr = fminf(fmaxf(wr, -are), are);
+              wi = fminf(fmaxf(wi, -aim), aim);
+              const float dr0 = wr - zr[lu];
+              const float di0 = wi - zi[lu];
+              if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+              const int owner = (lane & ~1) | oh;
+              const float dr = __shfl_sync(kFullMask, dr0, owner);
+              const float di = __shfl_sync(kFullMask, di0, owner);
+              // q <- q - G[:, u] dz for my users, with G[j][u] = conj(G[u][j])
+              const float4* gre = reinterpret_cast<const float4*>(sg + tma_gre<NU>(u, hf * UP));
+              const float4* gim = reinterpret_cast<const float4*>(sg + tma_gim<NU>(u, hf * UP));
 #pragma unroll
-            for (int l4 = 0; l4 < UP / 4; ++l4) {
-              const float4 r4 = gre[l4], i4 = gim[l4];
-              const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
+              for (int l4 = 0; l4 < UP / 4; ++l4) {
+                const float4 r4 = gre[l4], i4 = gim[l4];
+                const float gx[4] = {r4.x, r4.y, r4.z, r4.w}, gy[4] = {i4.x, i4.y, i4.z, i4.w};
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int l = 4 * l4 + c;
-                qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
-                qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
+                for (int c = 0; c < 4; ++c) {
+                  const int l = 4 * l4 + c;
+                  qr[l] = fmaf(-gx[c], dr, fmaf(-gy[c], di, qr[l]));
+                  qi[l] = fmaf(-gx[c], di, fmaf(gy[c], dr, qi[l]));
+                }
               }
             }
           }
         }
-      }
+      };
+      if (U == NU) sweeps(std::true_type{});
+      else sweeps(std::false_type{});
       __syncwarp();
       if (act) {
         float4* z4 = reinterpret_cast<float4*>(sq + tma_sq<NU>(ts, hf * UP));  // z overwrites q0

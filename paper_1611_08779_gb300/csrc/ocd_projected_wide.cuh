@@ -179,6 +179,10 @@ __device__ __forceinline__ void wide_outputs(const DetectParams& P, const float*
 // lane = 2 ts + hf owns users [hf*16, hf*16 + 16) of symbol ts.  G is in sg
 // (wide_gre / wide_gim rows), (d^-1, p, rho~ step^2, LLR level scale) per
 // user in spre.  Shared by the warp-level and the tcgen05 32-user kernels.
+// FULL_TILE: also compile the sweeps of a full user tile without per-user
+// guards (faster, more registers: the tcgen05 kernel's 128-register budget
+// takes the guarded form only).
+template <bool FULL_TILE = true>
 __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float* sq,
                                                     const float* sg, const float* spre,
                                                     long long sc, int tb, int np) {
@@ -210,53 +214,60 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
     }
     const float are = P.box ? P.box_a : __int_as_float(0x7f800000);
     const float aim = P.box ? (P.bpsk ? 0.0f : P.box_a) : __int_as_float(0x7f800000);
-    for (int k = 0; k < P.K; ++k) {
+    // a full user tile (U equal to the tile) needs no per-user guard: the
+    // updates of all users form one block the scheduler can interleave
+    auto sweeps = [&](auto fullc) {
+      constexpr bool FULL = decltype(fullc)::value;
+      for (int k = 0; k < P.K; ++k) {
 #pragma unroll 1
-      for (int oh = 0; oh < 2; ++oh) {
+        for (int oh = 0; oh < 2; ++oh) {
 #pragma unroll
-      for (int lu = 0; lu < UP; ++lu) {
-        const int u = oh * UP + lu;
-        if (u < U) {
-          const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
-          float q0, q1, p0, p1;
-          f2_unpack(QR[lu >> 1], q0, q1);
-          f2_unpack(QI[lu >> 1], p0, p1);
-          const float qr = (lu & 1) ? q1 : q0;
-          const float qi = (lu & 1) ? p1 : p0;
-          float wr = fmaf(dp.x, qr, dp.y * zr[lu]);
-          float wi = fmaf(dp.x, qi, dp.y * zi[lu]);
-          wr = fminf(fmaxf(wr, -are), are);
-          wi = fminf(fmaxf(wi, -aim), aim);
-          const float dr0 = wr - zr[lu];
-          const float di0 = wi - zi[lu];
-          if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
-          const int owner = (lane & ~1) | oh;
-          const float dr = __shfl_sync(kFullMask, dr0, owner);
-          const float di = __shfl_sync(kFullMask, di0, owner);
-          const unsigned long long DR = f2_pack(dr, dr);
-          const unsigned long long NDR = f2_pack(-dr, -dr);
-          const unsigned long long NDI = f2_pack(-di, -di);
-          const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
-          const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
+        for (int lu = 0; lu < UP; ++lu) {
+          const int u = oh * UP + lu;
+          if (FULL || u < U) {
+            const float2 dp = *reinterpret_cast<const float2*>(spre + 4 * u);  // (d^-1, p)
+            float q0, q1, p0, p1;
+            f2_unpack(QR[lu >> 1], q0, q1);
+            f2_unpack(QI[lu >> 1], p0, p1);
+            const float qr = (lu & 1) ? q1 : q0;
+            const float qi = (lu & 1) ? p1 : p0;
+            float wr = fmaf(dp.x, qr, dp.y * zr[lu]);
+            float wi = fmaf(dp.x, qi, dp.y * zi[lu]);
+            wr = fminf(fmaxf(wr, -are), are);
+            wi = fminf(fmaxf(wi, -aim), aim);
+            const float dr0 = wr - zr[lu];
+            const float di0 = wi - zi[lu];
+            if (hf == oh) { zr[lu] = wr; zi[lu] = wi; }
+            const int owner = (lane & ~1) | oh;
+            const float dr = __shfl_sync(kFullMask, dr0, owner);
+            const float di = __shfl_sync(kFullMask, di0, owner);
+            const unsigned long long DR = f2_pack(dr, dr);
+            const unsigned long long NDR = f2_pack(-dr, -dr);
+            const unsigned long long NDI = f2_pack(-di, -di);
+            const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
+            const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
 #pragma unroll
-          for (int l4 = 0; l4 < UP / 4; ++l4) {
-            const float4 r4 = gre[l4], i4 = gim[l4];
-            const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
-            const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
-            // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
-            f2_fma(QR[2 * l4], im0, NDI);
-            f2_fma(QR[2 * l4], re0, NDR);
-            f2_fma(QI[2 * l4], im0, DR);
-            f2_fma(QI[2 * l4], re0, NDI);
-            f2_fma(QR[2 * l4 + 1], im1, NDI);
-            f2_fma(QR[2 * l4 + 1], re1, NDR);
-            f2_fma(QI[2 * l4 + 1], im1, DR);
-            f2_fma(QI[2 * l4 + 1], re1, NDI);
+            for (int l4 = 0; l4 < UP / 4; ++l4) {
+              const float4 r4 = gre[l4], i4 = gim[l4];
+              const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
+              const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
+              // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
+              f2_fma(QR[2 * l4], im0, NDI);
+              f2_fma(QR[2 * l4], re0, NDR);
+              f2_fma(QI[2 * l4], im0, DR);
+              f2_fma(QI[2 * l4], re0, NDI);
+              f2_fma(QR[2 * l4 + 1], im1, NDI);
+              f2_fma(QR[2 * l4 + 1], re1, NDR);
+              f2_fma(QI[2 * l4 + 1], im1, DR);
+              f2_fma(QI[2 * l4 + 1], re1, NDI);
+            }
           }
         }
+        }
       }
-      }
-    }
+    };
+    if (FULL_TILE && U == NU) sweeps(std::integral_constant<bool, FULL_TILE>{});
+    else sweeps(std::false_type{});
     __syncwarp();
     if (act) {
       float4* z4 = reinterpret_cast<float4*>(sq + wide_sq(ts, hf * UP));
