@@ -250,7 +250,17 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
         }
       }
     };
-    if (first) {
+    if (bb == BB) {
+      // full block: a compile-time k-step loop, so the loads of one k-step
+      // can be issued under the MMAs of the one before
+      if (first) {
+#pragma unroll
+        for (int kb = 0; kb < BB; kb += 8) kstep(kb, std::true_type{});
+      } else {
+#pragma unroll
+        for (int kb = 0; kb < BB; kb += 8) kstep(kb, std::false_type{});
+      }
+    } else if (first) {
       for (int kb = 0; kb < bb; kb += 8) kstep(kb, std::true_type{});
     } else {
       for (int kb = 0; kb < bb; kb += 8) kstep(kb, std::false_type{});
