@@ -246,20 +246,45 @@ __device__ __forceinline__ void wide_sweeps_outputs(const DetectParams& P, float
             const unsigned long long NDI = f2_pack(-di, -di);
             const float4* gre = reinterpret_cast<const float4*>(sg + wide_gre(u, hf * UP));
             const float4* gim = reinterpret_cast<const float4*>(sg + wide_gim(u, hf * UP));
+            if constexpr (FULL) {
+              // a full tile first updates the pair that holds the next user
+              // (the next update's input); every q keeps its own operations
+              // and their order (the guarded form below measured faster in
+              // the slot order of its loads)
+              unsigned long long RE[UP / 2], IM[UP / 2];
 #pragma unroll
-            for (int l4 = 0; l4 < UP / 4; ++l4) {
-              const float4 r4 = gre[l4], i4 = gim[l4];
-              const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
-              const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
-              // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
-              f2_fma(QR[2 * l4], im0, NDI);
-              f2_fma(QR[2 * l4], re0, NDR);
-              f2_fma(QI[2 * l4], im0, DR);
-              f2_fma(QI[2 * l4], re0, NDI);
-              f2_fma(QR[2 * l4 + 1], im1, NDI);
-              f2_fma(QR[2 * l4 + 1], re1, NDR);
-              f2_fma(QI[2 * l4 + 1], im1, DR);
-              f2_fma(QI[2 * l4 + 1], re1, NDI);
+              for (int l4 = 0; l4 < UP / 4; ++l4) {
+                const float4 r4 = gre[l4], i4 = gim[l4];
+                RE[2 * l4] = f2_pack(r4.x, r4.y);
+                RE[2 * l4 + 1] = f2_pack(r4.z, r4.w);
+                IM[2 * l4] = f2_pack(i4.x, i4.y);
+                IM[2 * l4 + 1] = f2_pack(i4.z, i4.w);
+              }
+#pragma unroll
+              for (int j = 0; j < UP / 2; ++j) {
+                const int l2 = (((lu + 1) % UP) / 2 + j) % (UP / 2);
+                // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
+                f2_fma(QR[l2], IM[l2], NDI);
+                f2_fma(QR[l2], RE[l2], NDR);
+                f2_fma(QI[l2], IM[l2], DR);
+                f2_fma(QI[l2], RE[l2], NDI);
+              }
+            } else {
+#pragma unroll
+              for (int l4 = 0; l4 < UP / 4; ++l4) {
+                const float4 r4 = gre[l4], i4 = gim[l4];
+                const unsigned long long re0 = f2_pack(r4.x, r4.y), re1 = f2_pack(r4.z, r4.w);
+                const unsigned long long im0 = f2_pack(i4.x, i4.y), im1 = f2_pack(i4.z, i4.w);
+                // qr <- fma(-gx, dr, fma(-gy, di, qr)); qi <- fma(-gx, di, fma(gy, dr, qi))
+                f2_fma(QR[2 * l4], im0, NDI);
+                f2_fma(QR[2 * l4], re0, NDR);
+                f2_fma(QI[2 * l4], im0, DR);
+                f2_fma(QI[2 * l4], re0, NDI);
+                f2_fma(QR[2 * l4 + 1], im1, NDI);
+                f2_fma(QR[2 * l4 + 1], re1, NDR);
+                f2_fma(QI[2 * l4 + 1], im1, DR);
+                f2_fma(QI[2 * l4 + 1], re1, NDI);
+              }
             }
           }
         }
