@@ -384,6 +384,50 @@ int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const flo
                           const void* dxhat, const float* dllr, float* domega, float* dalpha,
                           void* workspace, size_t workspace_bytes, int algo, cudaStream_t stream);
 
+/*
+ * Fused training loss of the unfolded form: the mean binary cross-entropy of
+ * bit labels under P(b = 1) = sigmoid(L) over all N = Nsc*T*U*Q LLRs L of
+ * Eq. 9 (L > 0 favours bit 1):
+ *     loss = (1/N) sum [max(L, 0) - y L + log(1 + exp(-|L|))],
+ *     d loss / d L = (sigmoid(L) - y) / N,
+ * computed by the forward kernel where each LLR is formed, so that no
+ * separate loss kernels run between the forward and the adjoint.  The same
+ * function of the LLRs as binary_cross_entropy_with_logits with mean
+ * reduction.
+ *
+ * ocd_unfolded_bce_forward -- ocd_unfolded_forward plus the loss.
+ *   bits        device float [Nsc][T][U][Q]: labels y in [0, 1], the bit
+ *               order of the LLRs.
+ *   llr         device float [Nsc][T][U][Q] or NULL (the LLRs themselves).
+ *   dllr        device float [Nsc][T][U][Q]: d loss / d L (the adjoint input
+ *               of ocd_unfolded_bce_backward).
+ *   loss        device float [1]: the mean loss; 0 for an empty batch.
+ *   workspace   ocd_unfolded_workspace_size(Nsc, T, K) device bytes, 4-byte
+ *               aligned (per-sample loss sums, added in a fixed order: the
+ *               loss is deterministic).
+ * Other arguments as ocd_unfolded_forward.
+ */
+int ocd_unfolded_bce_forward(const void* H, const void* Y, int Nsc, int B, int U, int T,
+                             const float* N0, float Es, int K, int mode, int qam_order,
+                             const float* omega, const float* alpha, const float* bits,
+                             void* xhat, float* llr, float* dllr, float* loss, void* ckpt,
+                             void* workspace, size_t workspace_bytes, int algo,
+                             cudaStream_t stream);
+
+/*
+ * ocd_unfolded_bce_backward -- d loss / d omega and d loss / d alpha of the
+ * fused loss, times dloss (device float [1], the adjoint of the loss; NULL
+ * means 1): ocd_unfolded_backward with dxhat = NULL and dllr the forward's
+ * output, the scale applied to the summed gradients.  Arguments as
+ * ocd_unfolded_backward.
+ */
+int ocd_unfolded_bce_backward(const void* H, int Nsc, int B, int U, int T, const float* N0,
+                              float Es, int K, int mode, int qam_order, const float* omega,
+                              const float* alpha, const void* xhat, const void* ckpt,
+                              const float* dllr, const float* dloss, float* domega,
+                              float* dalpha, void* workspace, size_t workspace_bytes, int algo,
+                              cudaStream_t stream);
+
 /* Message describing the last non-OK status returned on the calling thread. */
 const char* ocd_last_error(void);
 

@@ -10,4 +10,4 @@ from .api import (bits_per_symbol, fault_status, make_staging, ocd_detect,  # no
 from .batched import (BatchedGraph, Cell, Tune, make_cell, make_workspace,  # noqa: F401
                       ocd_autotune_batched, ocd_detect_batched, ocd_detect_batched_static)
 from .shard import shard_range  # noqa: F401
-from .unfolded import UnfoldedOCD, unfolded_ocd  # noqa: F401
+from .unfolded import UnfoldedBCE, UnfoldedOCD, unfolded_bce_loss, unfolded_ocd  # noqa: F401

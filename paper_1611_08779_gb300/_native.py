@@ -83,6 +83,10 @@ SIGNATURES = {
                                   _vp, _vp, _i, _vp]),
     "ocd_unfolded_backward": (_i, [_vp, _i, _i, _i, _i, _vp, _f, _i, _i, _i, _vp, _vp, _vp, _vp,
                                    _vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
+    "ocd_unfolded_bce_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _f, _i, _i, _i, _vp, _vp,
+                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
+    "ocd_unfolded_bce_backward": (_i, [_vp, _i, _i, _i, _i, _vp, _f, _i, _i, _i, _vp, _vp, _vp,
+                                       _vp, _vp, _vp, _vp, _vp, _vp, _sz, _i, _vp]),
     "ocd_fault_status": (_i, [_i]),
     "ocd_wait_selftest": (_i, [_i, _vp]),
     "ocd_last_error": (ctypes.c_char_p, []),

@@ -71,6 +71,43 @@ __device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) 
   p = d * n;
 }
 
+// Binary cross-entropy of a label y in [0, 1] under P(b = 1) = sigmoid(L),
+// in the form that cannot overflow: max(L, 0) - y L + log(1 + exp(-|L|)).
+__device__ __forceinline__ float bce_term(float L, float y) {
+  return fmaxf(L, 0.0f) - y * L + log1pf(expf(-fabsf(L)));
+}
+// sigmoid(L) = 1 / (1 + exp(-L)), from exp(-|L|) so that it cannot overflow.
+__device__ __forceinline__ float sigmoid_of(float L) {
+  const float e = expf(-fabsf(L));
+  return L >= 0.0f ? 1.0f / (1.0f + e) : e / (1.0f + e);
+}
+
+// Soft output of item o = (sample, user): Eq. 9 with mu~ = p and rho~ =
+// ||h||^2 Es / n0.  The LLRs go to P.llr when requested and, with the fused
+// loss (P.bits), d loss / d L = (sigmoid(L) - y) / N to P.gllr.  Returns the
+// item's loss summed over its Q bits in order (0 without the fused loss).
+__device__ __forceinline__ float soft_output(const UnfoldParams& P, long long o, float2 z,
+                                             float nrm, float p, float n0) {
+  DetectParams D = P.D;
+  D.rho_scale = P.es / n0;
+  const int Q = P.D.Q;
+  if (!P.bits) {
+    if (P.llr) user_llr(z, nrm, p, D, P.llr + o * Q);
+    return 0.0f;
+  }
+  float* g = P.gllr + o * Q;
+  user_llr(z, nrm, p, D, g);  // the LLRs, in the slots of their derivatives
+  float acc = 0.0f;
+  for (int b = 0; b < Q; ++b) {
+    const float L = g[b];
+    const float y = __ldg(P.bits + o * Q + b);
+    if (P.llr) P.llr[o * Q + b] = L;
+    acc += bce_term(L, y);
+    g[b] = (sigmoid_of(L) - y) * P.inv_n;
+  }
+  return acc;
+}
+
 // Lane mapping for copying a row-major [n][U] complex array with a warp:
 // `rows` = max(1, 32 / U) rows per step, lane -> row r0 (< rows for an
 // active lane) and column u.
@@ -216,16 +253,19 @@ ocd_unfolded_forward_kernel(const __grid_constant__ UnfoldParams P) {
       if (lane < P.U) ck[P.B + lane] = z;
       W.template sweep<false>(r, z, nrm, __ldg(P.omega + k), __ldg(P.alpha + k), zb, qs);
     }
+    float lsum = 0.0f;
     if (lane < P.U) {
       const long long o = s * P.U + lane;
       P.xhat[o] = z;
-      if (P.llr) {
+      if (P.llr || P.bits) {
         float d, p;
         gains(nrm, __ldg(P.alpha + P.K - 1), d, p);
-        DetectParams D = P.D;
-        D.rho_scale = P.es / __ldg(P.N0 + w);
-        user_llr(z, nrm, p, D, P.llr + o * P.D.Q);
+        lsum = soft_output(P, o, z, nrm, p, __ldg(P.N0 + w));
       }
+    }
+    if (P.bits) {
+      const float ls = warp_sum(lsum);
+      if (lane == 0) P.lpart[s] = ls;
     }
   }
 }
@@ -386,10 +426,12 @@ ocd_unfolded_backward_kernel(const __grid_constant__ UnfoldParams P) {
   }
 }
 
-// out[j] = sum over samples of partial[s][j], j < 2K, in a fixed order.
+// out[j] = sum over samples of partial[s][j], j < 2K, in a fixed order,
+// times *gscale when it is given.
 __global__ void __launch_bounds__(256)
 ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples, int K,
-                           float* __restrict__ domega, float* __restrict__ dalpha) {
+                           const float* __restrict__ gscale, float* __restrict__ domega,
+                           float* __restrict__ dalpha) {
   __shared__ float red[256];
   const int j = blockIdx.x;  // 0 .. 2K-1
   float acc = 0.0f;
@@ -401,9 +443,26 @@ ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    if (j & 1) dalpha[j >> 1] = red[0];
-    else domega[j >> 1] = red[0];
+    const float v = gscale ? red[0] * *gscale : red[0];
+    if (j & 1) dalpha[j >> 1] = v;
+    else domega[j >> 1] = v;
   }
+}
+
+// *loss = scale * (sum over samples of part[s]), in a fixed order.
+__global__ void __launch_bounds__(256)
+ocd_unfolded_loss_kernel(const float* __restrict__ part, long long samples, float scale,
+                         float* __restrict__ loss) {
+  __shared__ float red[256];
+  float acc = 0.0f;
+  for (long long s = threadIdx.x; s < samples; s += blockDim.x) acc += part[s];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = red[0] * scale;
 }
 
 // ---------------------------------------------------------------------------
@@ -659,16 +718,19 @@ ocd_unfolded_proj_forward_kernel(const __grid_constant__ UnfoldParams P) {
       gains(nrm, __ldg(P.alpha + k), d, p);
       qsweep<false>(P, sG, gst, lane, q, z, d, p, __ldg(P.omega + k), zb, qs);
     }
+    float lsum = 0.0f;
     if (lane < U) {
       const long long o = s * U + lane;
       P.xhat[o] = z;
-      if (P.llr) {
+      if (P.llr || P.bits) {
         float d, p;
         gains(nrm, __ldg(P.alpha + P.K - 1), d, p);
-        DetectParams D = P.D;
-        D.rho_scale = P.es / __ldg(P.N0 + w);
-        user_llr(z, nrm, p, D, P.llr + o * P.D.Q);
+        lsum = soft_output(P, o, z, nrm, p, __ldg(P.N0 + w));
       }
+    }
+    if (P.bits) {
+      const float ls = warp_sum(lsum);
+      if (lane == 0) P.lpart[s] = ls;
     }
     __syncwarp();  // sG and sy are rewritten by the next sample
   }
@@ -880,16 +942,19 @@ ocd_unfolded_proj_forward_pair_kernel(const __grid_constant__ UnfoldParams P) {
       gains(nrm, __ldg(P.alpha + k), d, p);
       qsweep16<false>(P, sGh, gst, j, q, z, d, p, __ldg(P.omega + k), zb, qs);
     }
+    float lsum = 0.0f;
     if (act) {
       const long long o = s * U + j;
       P.xhat[o] = z;
-      if (P.llr) {
+      if (P.llr || P.bits) {
         float d, p;
         gains(nrm, __ldg(P.alpha + P.K - 1), d, p);
-        DetectParams D = P.D;
-        D.rho_scale = P.es / __ldg(P.N0 + s / P.T);
-        user_llr(z, nrm, p, D, P.llr + o * P.D.Q);
+        lsum = soft_output(P, o, z, nrm, p, __ldg(P.N0 + s / P.T));
       }
+    }
+    if (P.bits) {
+      const float ls = half_sum(lsum);  // over this half's users, in the warp_sum order
+      if (j == 0 && valid) P.lpart[s] = ls;
     }
     __syncwarp();  // sG and sq are rewritten by the next pair
   }
@@ -1148,9 +1213,14 @@ cudaError_t launch_unfolded(const UnfoldParams& P, bool backward, int sms, cudaS
   else if (na <= 4) e = launch_pair<4>(P, backward, (unsigned)grid, stream);
   else if (na <= 8) e = launch_pair<8>(P, backward, (unsigned)grid, stream);
   else e = launch_pair<16>(P, backward, (unsigned)grid, stream);
-  if (e != cudaSuccess || !backward) return e;
-  ocd_unfolded_reduce_kernel<<<2 * P.K, 256, 0, stream>>>(P.partial, P.samples, P.K, P.domega,
-                                                          P.dalpha);
+  if (e != cudaSuccess) return e;
+  if (!backward) {
+    if (!P.bits) return e;
+    ocd_unfolded_loss_kernel<<<1, 256, 0, stream>>>(P.lpart, P.samples, P.inv_n, P.loss);
+    return cudaGetLastError();
+  }
+  ocd_unfolded_reduce_kernel<<<2 * P.K, 256, 0, stream>>>(P.partial, P.samples, P.K, P.gscale,
+                                                          P.domega, P.dalpha);
   return cudaGetLastError();
 }
 
@@ -1225,6 +1295,14 @@ int sms_of_current(int& sms) {
   return OCD_OK;
 }
 
+// Adjoint and reduction; gscale (device float or null) multiplies the summed
+// parameter gradients.
+int unfolded_backward(const void* H, int Nsc, int B, int U, int T, const float* N0, float Es,
+                      int K, int mode, int qam_order, const float* omega, const float* alpha,
+                      const void* xhat, const void* ckpt, const void* dxhat, const float* dllr,
+                      const float* gscale, float* domega, float* dalpha, void* workspace,
+                      size_t workspace_bytes, int algo, cudaStream_t stream);
+
 }  // namespace
 
 extern "C" {
@@ -1270,6 +1348,72 @@ int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const flo
                           const float* alpha, const void* xhat, const void* ckpt,
                           const void* dxhat, const float* dllr, float* domega, float* dalpha,
                           void* workspace, size_t workspace_bytes, int algo, cudaStream_t stream) {
+  return unfolded_backward(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt,
+                           dxhat, dllr, nullptr, domega, dalpha, workspace, workspace_bytes, algo,
+                           stream);
+}
+
+int ocd_unfolded_bce_forward(const void* H, const void* Y, int Nsc, int B, int U, int T,
+                             const float* N0, float Es, int K, int mode, int qam_order,
+                             const float* omega, const float* alpha, const float* bits,
+                             void* xhat, float* llr, float* dllr, float* loss, void* ckpt,
+                             void* workspace, size_t workspace_bytes, int algo,
+                             cudaStream_t stream) {
+  ocd::UnfoldParams P;
+  int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt,
+                           algo, P);
+  if (st != OCD_OK) return st;
+  if (!loss) return fail(OCD_ERR_ARG, "loss must not be NULL");
+  if (P.samples > 0 && (!Y || !bits || !dllr))
+    return fail(OCD_ERR_ARG, "Y, bits and dllr must not be NULL");
+  if (((uintptr_t)Y & 7u) || (((uintptr_t)llr | (uintptr_t)bits | (uintptr_t)dllr |
+                               (uintptr_t)loss | (uintptr_t)workspace) & 3u))
+    return fail(OCD_ERR_ARG, "arrays must be aligned to their element size");
+  if (P.samples == 0) {
+    const cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    return OCD_OK;
+  }
+  if (!workspace || workspace_bytes < ocd_unfolded_workspace_size(Nsc, T, K))
+    return fail(OCD_ERR_ARG, "workspace of %zu bytes is smaller than the %zu needed",
+                workspace_bytes, ocd_unfolded_workspace_size(Nsc, T, K));
+  P.Y = static_cast<const float2*>(Y);
+  P.llr = llr;
+  P.bits = bits;
+  P.gllr = dllr;
+  P.lpart = static_cast<float*>(workspace);
+  P.loss = loss;
+  P.inv_n = (float)(1.0 / ((double)P.samples * U * P.D.Q));
+  int sms = 0;
+  st = sms_of_current(sms);
+  if (st != OCD_OK) return st;
+  const cudaError_t e = ocd::launch_unfolded(P, false, sms, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "unfolded forward launch");
+  return OCD_OK;
+}
+
+int ocd_unfolded_bce_backward(const void* H, int Nsc, int B, int U, int T, const float* N0,
+                              float Es, int K, int mode, int qam_order, const float* omega,
+                              const float* alpha, const void* xhat, const void* ckpt,
+                              const float* dllr, const float* dloss, float* domega,
+                              float* dalpha, void* workspace, size_t workspace_bytes, int algo,
+                              cudaStream_t stream) {
+  if ((long long)Nsc * T > 0 && !dllr) return fail(OCD_ERR_ARG, "dllr must not be NULL");
+  if ((uintptr_t)dloss & 3u) return fail(OCD_ERR_ARG, "arrays must be aligned to their element size");
+  return unfolded_backward(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt,
+                           nullptr, dllr, dloss, domega, dalpha, workspace, workspace_bytes, algo,
+                           stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int unfolded_backward(const void* H, int Nsc, int B, int U, int T, const float* N0, float Es,
+                      int K, int mode, int qam_order, const float* omega, const float* alpha,
+                      const void* xhat, const void* ckpt, const void* dxhat, const float* dllr,
+                      const float* gscale, float* domega, float* dalpha, void* workspace,
+                      size_t workspace_bytes, int algo, cudaStream_t stream) {
   ocd::UnfoldParams P;
   int st = unfolded_common(H, Nsc, B, U, T, N0, Es, K, mode, qam_order, omega, alpha, xhat, ckpt,
                            algo, P);
@@ -1290,6 +1434,7 @@ int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const flo
   }
   P.dxhat = static_cast<const float2*>(dxhat);
   P.dllr = dllr;
+  P.gscale = gscale;
   P.partial = static_cast<float*>(workspace);
   P.domega = domega;
   P.dalpha = dalpha;
@@ -1301,4 +1446,4 @@ int ocd_unfolded_backward(const void* H, int Nsc, int B, int U, int T, const flo
   return OCD_OK;
 }
 
-}  // extern "C"
+}  // namespace

@@ -22,6 +22,12 @@ struct UnfoldParams {
   float* __restrict__ partial;          // [Nsc*T][2K] per-sample parameter adjoints
   float* __restrict__ domega;           // [K] outputs of the adjoint
   float* __restrict__ dalpha;
+  const float* __restrict__ bits;       // [Nsc][T][U][Q] labels of the fused loss, or null (forward)
+  float* __restrict__ gllr;             // fused loss: d loss / d LLR (forward output)
+  float* __restrict__ lpart;            // fused loss: [Nsc*T] per-sample loss sums (forward)
+  float* __restrict__ loss;             // fused loss: the mean (forward output, one float)
+  const float* __restrict__ gscale;     // factor of the summed parameter gradients, or null (1)
+  float inv_n;                          // fused loss: 1 / (Nsc T U Q)
   long long samples;                    // Nsc * T
   int Nsc, B, U, T, K;
   float es;

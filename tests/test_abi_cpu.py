@@ -103,6 +103,26 @@ def test_host_entry_point_validates(lib):
     assert st == _native.OCD_ERR_ARG and "staging" in lib.ocd_last_error().decode()
 
 
+def test_fused_loss_entry_points_validate(lib):
+    """The fused-loss calls check their extra arguments before any device work."""
+    def fwd(bits=FAKE, dllr=FAKE, loss=FAKE, ws=FAKE, ws_bytes=1 << 20):
+        return lib.ocd_unfolded_bce_forward(FAKE, FAKE, 4, 16, 4, 2, FAKE, 1.0, 3, 1, 16, FAKE,
+                                            FAKE, bits, FAKE, None, dllr, loss, FAKE, ws,
+                                            ws_bytes, 0, None)
+    assert fwd(loss=None) == _native.OCD_ERR_ARG
+    assert "loss must not be NULL" in lib.ocd_last_error().decode()
+    for kw in (dict(bits=None), dict(dllr=None)):
+        assert fwd(**kw) == _native.OCD_ERR_ARG
+        assert "bits and dllr" in lib.ocd_last_error().decode()
+    assert fwd(ws_bytes=16) == _native.OCD_ERR_ARG
+    assert "workspace" in lib.ocd_last_error().decode()
+    assert fwd(bits=FAKE + 2) == _native.OCD_ERR_ARG
+    assert "aligned" in lib.ocd_last_error().decode()
+    st = lib.ocd_unfolded_bce_backward(FAKE, 4, 16, 4, 2, FAKE, 1.0, 3, 1, 16, FAKE, FAKE, FAKE,
+                                       FAKE, None, None, FAKE, FAKE, FAKE, 1 << 20, 0, None)
+    assert st == _native.OCD_ERR_ARG and "dllr" in lib.ocd_last_error().decode()
+
+
 def test_error_message_is_per_thread(lib):
     import threading
     call(lib, U=99)

@@ -323,3 +323,116 @@ def test_a_few_training_steps_reduce_the_loss():
         losses.append(float(loss))
     assert losses[-1] < 0.8 * losses[0], losses
     assert all(math.isfinite(v) for v in losses)
+
+
+# ---------------------------------------------------------------------------
+# Fused training loss (ocd_unfolded_bce_forward / _backward): the mean BCE of
+# the bits and its LLR derivative formed in the forward kernel.
+# ---------------------------------------------------------------------------
+
+def fused_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t, arr="auto", scale=None):
+    o = torch.tensor(om, device="cuda", requires_grad=True)
+    a = torch.tensor(al, device="cuda", requires_grad=True)
+    loss, x, llr = ocd.unfolded_bce_loss(o, a, Hd, Yd, N0d, bits_t, 1.0, mode, order, algo=arr,
+                                         return_outputs=True)
+    (loss * scale if scale is not None else loss).backward()
+    return float(loss), o.grad.cpu().numpy(), a.grad.cpu().numpy(), x, llr
+
+
+@pytest.mark.parametrize("arr", ARR)
+@pytest.mark.parametrize("mode", ["box", "mmse"])
+@pytest.mark.parametrize("B,U,T,K,order", [(128, 16, 2, 5, 16), (48, 8, 4, 3, 64), (20, 3, 3, 2, 2),
+                                           (64, 32, 1, 3, 16), (33, 17, 2, 2, 256)])
+def test_fused_loss_matches_fp64_autograd(mode, B, U, T, K, order, arr):
+    """Loss and every omega_k, alpha_k gradient of the fused path against the
+    FP64 reference (oracle/unfolded.py: BCE of the Eq. 9 LLRs), with the
+    bound of the composable path.  The shapes reach every forward kernel:
+    two samples per warp (U <= 16, projected), one (U > 16, projected) and
+    the residual arrangement."""
+    H, Y, N0, bits = problem(32, B, U, T, order, seed=11 * B + U)
+    om, al = params(K, seed=U + 2 * K)
+    loss_ref, gom_ref, gal_ref = reference(H, Y, N0, om, al, mode, order, bits)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    loss, gom, gal, _, _ = fused_loss_grad(Hd, Yd, N0d, om, al, mode, order, bits_t, arr)
+    assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
+    assert_grad_close(gom, gom_ref, "d loss / d omega")
+    assert_grad_close(gal, gal_ref, "d loss / d alpha")
+
+
+@pytest.mark.parametrize("arr", ARR)
+def test_fused_loss_matches_the_composable_path(arr):
+    """Same inputs through unfolded_ocd + binary_cross_entropy_with_logits:
+    identical xhat and LLRs (the same kernels form them), the loss and the
+    gradients equal up to FP32 rounding (the loss terms are summed in another
+    order; d loss / d L = (sigmoid(L) - y) / N is rounded by each side)."""
+    H, Y, N0, bits = problem(300, 64, 8, 2, 16, seed=91)
+    om, al = params(4, seed=19)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    loss, gom, gal, x, llr = fused_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, arr)
+    o = torch.tensor(om, device="cuda", requires_grad=True)
+    a = torch.tensor(al, device="cuda", requires_grad=True)
+    x2, llr2 = ocd.unfolded_ocd(o, a, Hd, Yd, N0d, 1.0, "box", 16, algo=arr)
+    loss2 = torch.nn.functional.binary_cross_entropy_with_logits(llr2, bits_t)
+    loss2.backward()
+    assert torch.equal(torch.view_as_real(x), torch.view_as_real(x2))
+    assert torch.equal(llr, llr2)
+    assert abs(loss - float(loss2)) <= 1e-6 * abs(float(loss2))
+    np.testing.assert_allclose(gom, o.grad.cpu().numpy(), rtol=1e-4,
+                               atol=1e-5 * float(np.max(np.abs(gom))))
+    np.testing.assert_allclose(gal, a.grad.cpu().numpy(), rtol=1e-4,
+                               atol=1e-5 * float(np.max(np.abs(gal))))
+
+
+def test_fused_loss_at_the_training_batch_size():
+    """The benchmark's training step through the fused path: 4096 samples of
+    128x16, K = 5, 16-QAM, SNR 5-25 dB, OCD-BOX; loss and every omega_k,
+    alpha_k against FP64 autograd."""
+    H, Y, N0, bits = problem(4096, 128, 16, 1, 16, seed=21)
+    om, al = params(5, seed=9)
+    loss_ref, gom_ref, gal_ref = reference(H, Y, N0, om, al, "box", 16, bits)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    loss, gom, gal, _, _ = fused_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, "projected")
+    assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
+    assert_grad_close(gom, gom_ref, "d loss / d omega")
+    assert_grad_close(gal, gal_ref, "d loss / d alpha")
+
+
+def test_fused_loss_scales_with_the_incoming_gradient_and_is_deterministic():
+    H, Y, N0, bits = problem(256, 64, 8, 2, 16, seed=52)
+    om, al = params(3, seed=8)
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    r1 = fused_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    r2 = fused_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    assert r1[0] == r2[0] and np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+    r3 = fused_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t, scale=-2.5)
+    np.testing.assert_allclose(r3[1], -2.5 * r1[1], rtol=1e-6)
+    np.testing.assert_allclose(r3[2], -2.5 * r1[2], rtol=1e-6)
+
+
+def test_fused_loss_edge_cases():
+    """A zero channel column gives L = 0 (loss term log 2 per bit) and finite
+    gradients; an empty batch gives loss 0 and zero gradients."""
+    H, Y, N0, bits = problem(6, 16, 4, 2, 16, seed=72)
+    H[:, :, 2] = 0
+    om, al = params(2, seed=7)
+    al[:] = 0.0
+    Hd, Yd, N0d = to_dev(H, Y, N0)
+    bits_t = torch.from_numpy(bits.astype(np.float32)).cuda()
+    loss, gom, gal, x, llr = fused_loss_grad(Hd, Yd, N0d, om, al, "box", 16, bits_t)
+    assert torch.all(llr[:, :, 2] == 0) and math.isfinite(loss)
+    assert np.all(np.isfinite(gom)) and np.all(np.isfinite(gal))
+    ref = float(torch.nn.functional.binary_cross_entropy_with_logits(llr, bits_t))
+    assert abs(loss - ref) <= 1e-6 * ref
+    He = torch.empty((0, 16, 4), dtype=torch.complex64, device="cuda")
+    Ye = torch.empty((0, 2, 16), dtype=torch.complex64, device="cuda")
+    be = torch.empty((0, 2, 4, 4), dtype=torch.float32, device="cuda")
+    o = torch.tensor(om, device="cuda", requires_grad=True)
+    a = torch.tensor(al, device="cuda", requires_grad=True)
+    le = ocd.unfolded_bce_loss(o, a, He, Ye, torch.empty(0, device="cuda"), be, 1.0, "box", 16)
+    le.backward()
+    assert float(le) == 0.0
+    assert torch.all(o.grad == 0) and torch.all(a.grad == 0)
