@@ -63,6 +63,19 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(kFullMask, v.x, src), __shfl_sync(kFullMask, v.y, src));
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization (launch_pdl) may be scheduled before the kernel ahead of it
+// in the stream has finished; pdl_wait() returns once that kernel has
+// completed and its writes are visible (a no-op for a plain launch).
+// pdl_trigger(), issued after a CTA's last global write, lets the launch of
+// the kernel behind this one begin once every CTA has issued it or exited,
+// so a grid waiting in pdl_wait never holds slots that this grid still
+// needs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // d and p of sweep k for a user with squared norm n (0, 0 for a zero or
 // negative denominator).
 __device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) {
@@ -433,6 +446,7 @@ ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples,
                            const float* __restrict__ gscale, float* __restrict__ domega,
                            float* __restrict__ dalpha) {
   __shared__ float red[256];
+  pdl_wait();
   const int j = blockIdx.x;  // 0 .. 2K-1
   float acc = 0.0f;
   for (long long s = threadIdx.x; s < samples; s += blockDim.x) acc += partial[s * 2 * K + j];
@@ -447,6 +461,7 @@ ocd_unfolded_reduce_kernel(const float* __restrict__ partial, long long samples,
     if (j & 1) dalpha[j >> 1] = v;
     else domega[j >> 1] = v;
   }
+  pdl_trigger();
 }
 
 // *loss = scale * (sum over samples of part[s]), in a fixed order.
@@ -454,6 +469,7 @@ __global__ void __launch_bounds__(256)
 ocd_unfolded_loss_kernel(const float* __restrict__ part, long long samples, float scale,
                          float* __restrict__ loss) {
   __shared__ float red[256];
+  pdl_wait();
   float acc = 0.0f;
   for (long long s = threadIdx.x; s < samples; s += blockDim.x) acc += part[s];
   red[threadIdx.x] = acc;
@@ -463,6 +479,7 @@ ocd_unfolded_loss_kernel(const float* __restrict__ part, long long samples, floa
     __syncthreads();
   }
   if (threadIdx.x == 0) *loss = red[0] * scale;
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
@@ -900,6 +917,7 @@ template <int UT>
 __global__ void __launch_bounds__(128)
 ocd_unfolded_proj_forward_pair_kernel(const __grid_constant__ UnfoldParams P) {
   extern __shared__ float2 unf_smem[];
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int U = P.U, B = P.B;
   const int gst = U + 1;
@@ -958,11 +976,13 @@ ocd_unfolded_proj_forward_pair_kernel(const __grid_constant__ UnfoldParams P) {
     }
     __syncwarp();  // sG and sq are rewritten by the next pair
   }
+  pdl_trigger();
 }
 
 __global__ void __launch_bounds__(128)
 ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
   extern __shared__ float2 unf_smem[];
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int U = P.U;
   const int gst = U + 1;
@@ -1098,6 +1118,7 @@ ocd_unfolded_proj_backward_pair_kernel(const __grid_constant__ UnfoldParams P) {
       }
     }
   }
+  pdl_trigger();
 }
 
 // cudaFuncSetAttribute once per (device, kernel, size): the launches below
@@ -1114,6 +1135,26 @@ cudaError_t allow_smem(const void* fn, size_t smem) {
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) have = smem;
   return e;
+}
+
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the kernel ahead of it in the stream drains, and waits in pdl_wait()
+// for its results.  Only for kernels that call pdl_wait() before their first
+// read of another kernel's output.
+template <class... Params, class... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 constexpr int kProjFwdWarps = 2;  // warps per CTA of the projected forward kernel
@@ -1139,8 +1180,9 @@ cudaError_t launch_proj_fwd_pair(const UnfoldParams& P, cudaStream_t stream) {
   if (e != cudaSuccess) return e;
   const long long npairs = (P.samples + 1) / 2;
   const unsigned grid = (unsigned)((npairs + kProjFwdPairWarps - 1) / kProjFwdPairWarps);
-  ocd_unfolded_proj_forward_pair_kernel<UT><<<grid, 32 * kProjFwdPairWarps, smem, stream>>>(P);
-  return cudaGetLastError();
+  e = launch_pdl(ocd_unfolded_proj_forward_pair_kernel<UT>, grid, 32 * kProjFwdPairWarps, smem,
+                 stream, P);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // U <= 16: two samples per warp; larger U: one sample per warp.
@@ -1160,7 +1202,8 @@ cudaError_t launch_proj(const UnfoldParams& P, bool backward, unsigned grid, cud
   if (pair) {
     const long long need = ((P.samples + 1) / 2 + 3) / 4;  // 4 warps per CTA, a pair per warp
     if ((long long)grid > need) grid = (unsigned)need;
-    ocd_unfolded_proj_backward_pair_kernel<<<grid, 128, smem, stream>>>(P);
+    e = launch_pdl(ocd_unfolded_proj_backward_pair_kernel, grid, 128, smem, stream, P);
+    if (e != cudaSuccess) return e;
   } else {
     ocd_unfolded_proj_backward_kernel<<<grid, 128, smem, stream>>>(P);
   }
@@ -1216,12 +1259,13 @@ cudaError_t launch_unfolded(const UnfoldParams& P, bool backward, int sms, cudaS
   if (e != cudaSuccess) return e;
   if (!backward) {
     if (!P.bits) return e;
-    ocd_unfolded_loss_kernel<<<1, 256, 0, stream>>>(P.lpart, P.samples, P.inv_n, P.loss);
-    return cudaGetLastError();
+    e = launch_pdl(ocd_unfolded_loss_kernel, 1, 256, 0, stream, (const float*)P.lpart,
+                   P.samples, P.inv_n, P.loss);
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
-  ocd_unfolded_reduce_kernel<<<2 * P.K, 256, 0, stream>>>(P.partial, P.samples, P.K, P.gscale,
-                                                          P.domega, P.dalpha);
-  return cudaGetLastError();
+  e = launch_pdl(ocd_unfolded_reduce_kernel, (unsigned)(2 * P.K), 256, 0, stream,
+                 (const float*)P.partial, P.samples, P.K, P.gscale, P.domega, P.dalpha);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace ocd
