@@ -106,6 +106,35 @@ cudaError_t launch_projected_lane(const DetectParams& P, unsigned grid, cudaStre
 // after wait_ns and sets the fault word.  Exercises the timeout path.
 cudaError_t projected_tma_wait_selftest(unsigned long long wait_ns, cudaStream_t stream);
 
+// Programmatic dependent launch.  A kernel launched by launch_serialized may
+// be scheduled while the kernel ahead of it in the stream drains: pdl_wait()
+// returns once that kernel has completed and its writes are visible (a
+// no-op after a plain launch), so a kernel calls it before its first access
+// to global memory that another kernel may write.  pdl_trigger(), issued
+// after a CTA's last global write, lets the launch of the next kernel begin
+// once every CTA has issued it or exited, so a grid waiting in pdl_wait
+// never holds slots that this grid still needs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// cudaLaunchKernel with programmatic stream serialization (kernels that call
+// pdl_wait as above).
+inline cudaError_t launch_serialized(const void* fn, unsigned grid, unsigned block, void** args,
+                                     size_t smem, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // Projection onto C_O (Eq. 14): for square QAM clip real and imaginary parts
 // independently to [-a, a]; for BPSK clip the real part and zero the
 // imaginary part.  MMSE mode has C = C (identity).

@@ -58,8 +58,8 @@ cudaError_t launch_projected_h16(const DetectParams& P, unsigned grid, cudaStrea
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   DetectParams p = P;
   void* args[] = {&p, &map};
-  return cudaLaunchKernel(projected_h16_kernel_ptr(P.storage, P.U), dim3(grid), dim3(128), args,
-                          projected_h16_smem_per_cta(P.U), stream);
+  return launch_serialized(projected_h16_kernel_ptr(P.storage, P.U), grid, 128, args,
+                           projected_h16_smem_per_cta(P.U), stream);
 }
 
 cudaError_t projected_h16_fault(unsigned int* bits, bool clear) {

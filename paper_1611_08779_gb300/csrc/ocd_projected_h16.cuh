@@ -128,6 +128,7 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     fence_mbar_init();
   }
   __syncwarp();
+  pdl_wait();  // launched by launch_serialized
 
   struct Cursor {
     long long sc;
@@ -425,6 +426,7 @@ ocd_projected_h16_kernel(const DetectParams P, const __grid_constant__ CUtensorM
     }
     __syncwarp();
   }
+  pdl_trigger();
 }
 
 }  // namespace ocd

@@ -228,6 +228,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(base + S::kOffTmem);
+  pdl_wait();  // launched by launch_serialized
 #ifdef OCD_TC_TRACE
   unsigned long long tr[4] = {0, 0, 0, 0};
 #endif
@@ -508,6 +509,7 @@ ocd_projected_tc_kernel(const __grid_constant__ DetectParams P,
   if (lane == 0)
     for (int k = 0; k < 4; ++k) atomicAdd(&g_tc_trace[4 * warp + k], tr[k]);
 #endif
+  pdl_trigger();
 
   tc_fence_before();
   __syncthreads();

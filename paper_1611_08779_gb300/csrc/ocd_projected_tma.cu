@@ -86,8 +86,8 @@ cudaError_t launch_projected_tma(const DetectParams& P, unsigned grid, cudaStrea
   const cudaError_t e = encode_ymap_tma(P, &map, &p.ymap3d);
   if (e != cudaSuccess) return e;
   void* args[] = {&p, &map};
-  return cudaLaunchKernel(projected_tma_kernel_ptr(P.U), dim3(grid), dim3(projected_tma_threads()),
-                          args, projected_tma_smem_per_cta(P.U), stream);
+  return launch_serialized(projected_tma_kernel_ptr(P.U), grid, projected_tma_threads(), args,
+                           projected_tma_smem_per_cta(P.U), stream);
 }
 
 int tma_steps_per_sc(int B, int T) {

@@ -656,7 +656,11 @@ ocd_projected_tma_kernel(const __grid_constant__ DetectParams P,
   }
   __syncwarp();
   uint32_t parity = 0;  // bit i: parity of the next phase of buffer i
+  // launched by launch_serialized: the set-up above may overlap the drain of
+  // the kernel ahead in the stream
+  pdl_wait();
   tma_walk<UT>(P, &ymap, ws, bar0, parity, gw, P.Nsc, nW);
+  pdl_trigger();
 }
 
 // Several problems in one persistent launch: each warp draws tickets from a

@@ -19,8 +19,8 @@ cudaError_t launch_projected_wide(const DetectParams& P, unsigned grid, cudaStre
   if (e != cudaSuccess) return e;
   DetectParams p = P;
   void* args[] = {&p, &map};
-  return cudaLaunchKernel(projected_wide_kernel_ptr(), dim3(grid), dim3(WideShape::kThreads), args,
-                          projected_wide_smem_per_cta(), stream);
+  return launch_serialized(projected_wide_kernel_ptr(), grid, WideShape::kThreads, args,
+                           projected_wide_smem_per_cta(), stream);
 }
 
 const void* projected_tc_kernel_ptr(int T) {
@@ -40,8 +40,8 @@ cudaError_t launch_projected_tc(const DetectParams& P, unsigned grid, cudaStream
   if (e != cudaSuccess) return e;
   DetectParams p = P;
   void* args[] = {&p, &map};
-  return cudaLaunchKernel(projected_tc_kernel_ptr(P.T), dim3(grid), dim3(projected_tc_threads()),
-                          args, projected_tc_smem_per_cta(P.T), stream);
+  return launch_serialized(projected_tc_kernel_ptr(P.T), grid, projected_tc_threads(), args,
+                           projected_tc_smem_per_cta(P.T), stream);
 }
 
 bool wide_fuses(int T) { return OCD_WIDE_FUSE && T <= 8; }

@@ -695,10 +695,12 @@ ocd_projected_wide_kernel(const __grid_constant__ DetectParams P,
   }
   __syncwarp();
   uint32_t parity = 0;
+  pdl_wait();  // launched by launch_serialized
   if (OCD_WIDE_FUSE && P.T <= 8)
     wide_walk<true>(P, &ymap, ws, bar0, parity, gw, P.Nsc, gridDim.x);
   else
     wide_walk<false>(P, &ymap, ws, bar0, parity, gw, P.Nsc, gridDim.x);
+  pdl_trigger();
 }
 
 // Several problems: each warp draws tickets (runs of subcarriers of one

@@ -63,19 +63,6 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(kFullMask, v.x, src), __shfl_sync(kFullMask, v.y, src));
 }
 
-// Programmatic dependent launch.  A kernel launched with programmatic stream
-// serialization (launch_pdl) may be scheduled before the kernel ahead of it
-// in the stream has finished; pdl_wait() returns once that kernel has
-// completed and its writes are visible (a no-op for a plain launch).
-// pdl_trigger(), issued after a CTA's last global write, lets the launch of
-// the kernel behind this one begin once every CTA has issued it or exited,
-// so a grid waiting in pdl_wait never holds slots that this grid still
-// needs.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // d and p of sweep k for a user with squared norm n (0, 0 for a zero or
 // negative denominator).
 __device__ __forceinline__ void gains(float n, float alpha, float& d, float& p) {
@@ -1137,10 +1124,9 @@ cudaError_t allow_smem(const void* fn, size_t smem) {
   return e;
 }
 
-// Launch with programmatic stream serialization: the kernel may be scheduled
-// while the kernel ahead of it in the stream drains, and waits in pdl_wait()
-// for its results.  Only for kernels that call pdl_wait() before their first
-// read of another kernel's output.
+// Typed launch with programmatic stream serialization (see pdl_wait): only
+// for kernels that call pdl_wait() before their first read of another
+// kernel's output.
 template <class... Params, class... Args>
 cudaError_t launch_pdl(void (*kernel)(Params...), unsigned grid, unsigned block, size_t smem,
                        cudaStream_t stream, Args... args) {
