@@ -57,8 +57,8 @@ cudaError_t launch_projected_lane(const DetectParams& P, unsigned grid, cudaStre
   if (!fn) return cudaErrorInvalidValue;
   DetectParams p = P;
   void* args[] = {&p};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(projected_lane_threads()), args,
-                          projected_lane_smem_per_cta(P.U), stream);
+  return launch_serialized(fn, grid, projected_lane_threads(), args,
+                           projected_lane_smem_per_cta(P.U), stream);
 }
 
 }  // namespace ocd

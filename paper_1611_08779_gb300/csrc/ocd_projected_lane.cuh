@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(128, OCD_LANE_MIN_CTAS) ocd_projected_lane_ker
   const long long W = (long long)gridDim.x * S::kWarps;
   const long long first = (long long)blockIdx.x * S::kWarps + warp;
   if (first >= ngroups) return;  // whole warp; no CTA-wide barrier follows
+  pdl_wait();                      // launched by launch_serialized
   const int nchunk = (B + APC - 1) / APC;
   const long long nsteps = ((ngroups - 1 - first) / W + 1) * nchunk;
 
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(128, OCD_LANE_MIN_CTAS) ocd_projected_lane_ker
     buf = buf + 1 == S::kStages ? 0 : buf + 1;
   }
   lane_wait<0>();
+  pdl_trigger();
 }
 
 }  // namespace ocd
