@@ -139,3 +139,24 @@ def test_tie_at_the_box_bound_passes_no_gradient():
     assert complex(z[0, 0, 0]) == a
     z[0, 0, 0].real.backward()
     assert float(al.grad) == 0.0 and float(om.grad) == a
+
+
+def test_bce_loss_closed_forms():
+    """The training loss the fused path reproduces: the mean over all LLRs of
+    -log P(b) with P(b = 1) = 1 / (1 + exp(-L)), written out by hand for a
+    few logits and labels (L = 0 costs log 2 whatever the label; a confident
+    right answer costs almost nothing, a confident wrong one about |L|), and
+    its derivative (sigmoid(L) - y) / N."""
+    L = torch.tensor([[0.0, 2.0, -3.0], [40.0, -40.0, 0.5]], dtype=torch.float64,
+                     requires_grad=True)
+    y = np.array([[1, 1, 1], [0, 0, 1]], dtype=np.uint8)
+    loss = orc.bce_loss(L, y)
+    terms = [math.log(2.0), math.log1p(math.exp(-2.0)), 3.0 + math.log1p(math.exp(-3.0)),
+             40.0 + math.log1p(math.exp(-40.0)), math.log1p(math.exp(-40.0)),
+             math.log1p(math.exp(-0.5))]
+    assert abs(float(loss) - sum(terms) / 6.0) < 1e-14
+    loss.backward()
+    sig = lambda v: 1.0 / (1.0 + math.exp(-v))  # noqa: E731
+    want = [[(sig(0.0) - 1) / 6, (sig(2.0) - 1) / 6, (sig(-3.0) - 1) / 6],
+            [sig(40.0) / 6, sig(-40.0) / 6, (sig(0.5) - 1) / 6]]
+    assert np.max(np.abs(L.grad.numpy() - np.array(want))) < 1e-15
