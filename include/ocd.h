@@ -35,6 +35,11 @@
  * device entry points allocate nothing, never synchronize, and enqueue their
  * work on `stream` (0 = legacy default stream).  Errors are reported by the
  * return value; ocd_last_error() gives a message for the calling thread.
+ * Stream order holds as for any launch: the detection kernels and the
+ * unfolded form's paired kernels are launched with programmatic stream
+ * serialization, so their blocks may be placed while the work ahead of them
+ * in the stream drains, but they touch no global memory before it has
+ * completed.
  */
 #ifndef OCD_H_
 #define OCD_H_
