@@ -148,6 +148,22 @@ def test_binding_refuses_cpu_tensors():
         ocd.ocd_detect(H, Y, 0.1)
 
 
+def test_unfolded_bindings_refuse_cpu_tensors():
+    """Neither the composable nor the fused-loss unfolded call has a CPU path."""
+    torch = pytest.importorskip("torch")
+    import paper_1611_08779_gb300 as ocd
+    H = torch.zeros((2, 4, 2), dtype=torch.complex64)
+    Y = torch.zeros((2, 1, 4), dtype=torch.complex64)
+    om = torch.ones(3)
+    al = torch.zeros(3)
+    N0 = torch.ones(2)
+    bits = torch.zeros((2, 1, 2, 4))
+    with pytest.raises(ValueError, match="CUDA"):
+        ocd.unfolded_ocd(om, al, H, Y, N0, 1.0, "box", 16)
+    with pytest.raises(ValueError, match="CUDA"):
+        ocd.unfolded_bce_loss(om, al, H, Y, N0, bits, 1.0, "box", 16)
+
+
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError, match="not built"):
         saved = _native._lib
