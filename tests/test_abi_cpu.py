@@ -148,6 +148,34 @@ def test_binding_refuses_cpu_tensors():
         ocd.ocd_detect(H, Y, 0.1)
 
 
+def test_binding_argument_checks():
+    """The binding's own checks (before any library call): alphabets, modes,
+    storage types and layouts."""
+    torch = pytest.importorskip("torch")
+    from paper_1611_08779_gb300 import api
+    assert [api.bits_per_symbol(o) for o in (2, 4, 16, 64, 256)] == [1, 2, 4, 6, 8]
+    for bad in (8, 32, 1024, 0):
+        with pytest.raises(ValueError, match="qam_order"):
+            api.bits_per_symbol(bad)
+    assert api._mode("BOX") == _native.OCD_BOX and api._mode("mmse") == _native.OCD_MMSE
+    with pytest.raises(ValueError, match="mode"):
+        api._mode("zf")
+    assert api._storage_of("H", torch.zeros((2, 3, 4), dtype=torch.complex64)) == \
+        (_native.OCD_STORE_C64, (2, 3, 4))
+    assert api._storage_of("H", torch.zeros((2, 3, 4, 2), dtype=torch.bfloat16)) == \
+        (_native.OCD_STORE_BF16, (2, 3, 4))
+    assert api._storage_of("H", torch.zeros((2, 3, 4, 2), dtype=torch.float16)) == \
+        (_native.OCD_STORE_F16, (2, 3, 4))
+    with pytest.raises(TypeError, match="expected complex64"):
+        api._storage_of("H", torch.zeros((2, 3, 4), dtype=torch.float32))
+    with pytest.raises(TypeError, match="expected complex64"):
+        api._storage_of("H", torch.zeros((2, 3, 4, 3), dtype=torch.bfloat16))
+    with pytest.raises(ValueError, match="contiguous"):
+        api._storage_of("H", torch.zeros((4, 3), dtype=torch.complex64).t())
+    with pytest.raises(TypeError, match="complex64"):
+        api._check_c64("Y", torch.zeros(3, dtype=torch.complex128))
+
+
 def test_unfolded_bindings_refuse_cpu_tensors():
     """Neither the composable nor the fused-loss unfolded call has a CPU path."""
     torch = pytest.importorskip("torch")
